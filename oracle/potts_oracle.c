@@ -1,0 +1,324 @@
+/*
+ * Serial CPU oracle for the checkerboard Metropolis sweep of the 2D q-state
+ * Potts model.  TEST INFRASTRUCTURE ONLY: see potts_oracle.h.
+ *
+ * It is plain, slow and follows the method step by step:
+ *   - Hamiltonian H = -J sum_<ij> delta(s_i, s_j), J = 1, k_B = 1, periodic
+ *     L x L square lattice (Sec. 2.1, Eq. 1).  We track B = -H, the number of
+ *     satisfied bonds.
+ *   - Metropolis single-spin flip: the new state is drawn uniformly from all
+ *     q states and accepted with probability min(1, exp(-beta dE))
+ *     (Sec. 2.2 definition of an MCS, Sec. 3.2 on the random numbers needed).
+ *   - Checkerboard order: all white sites ((i+j) even) first, then all black
+ *     ones (Sec. 3); one sweep = one MCS = N trials.
+ *   - Acceptance against a per-temperature table of Boltzmann weights
+ *     (Sec. 5, the CPU code), here floor(2^32 exp(-beta d)) compared with a
+ *     32-bit uniform word.
+ *   - Energy and the q-state histogram are carried along incrementally while
+ *     spins change (Sec. 7 proposes accumulating the energy change on the
+ *     fly); a check mode recounts both from scratch after every sweep.
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), one call per group
+ * of four consecutive sites of one colour, one 32-bit word per site.
+ */
+#include "potts_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------------
+ * Philox4x32-10, from the SC'11 definition: each round multiplies counter
+ * words 0 and 2 by two fixed 32-bit constants (full 64-bit products), then
+ * forms the new counter (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0).  Between
+ * rounds the two key words advance by the Weyl constants (golden ratio and
+ * sqrt(3)-1 scaled to 2^32).  Ten rounds, nine key bumps.
+ * ------------------------------------------------------------------- */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                          uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += PHILOX_W0;
+      k1 += PHILOX_W1;
+    }
+    uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+uint32_t oracle_site_word(uint64_t seed, uint64_t sweep, uint32_t domain,
+                          uint64_t k) {
+  uint32_t ctr[4], key[2], out[4];
+  ctr[0] = (uint32_t)(k >> 2);
+  ctr[1] = (uint32_t)sweep;
+  ctr[2] = domain;
+  ctr[3] = (uint32_t)(sweep >> 32);
+  key[0] = (uint32_t)seed;
+  key[1] = (uint32_t)(seed >> 32);
+  oracle_philox4x32_10(ctr, key, out);
+  return out[k & 3u];
+}
+
+/* ---------------------------------------------------------------------
+ * Boltzmann table (Sec. 5): probability exp(-beta d) for an energy
+ * increase d = 1..4, as a 32-bit fixed-point threshold.
+ * ------------------------------------------------------------------- */
+int oracle_thresholds(double beta, uint64_t thr[5]) {
+  if (!(beta >= 0.0) || !isfinite(beta)) return -1;
+  thr[0] = (uint64_t)1 << 32;
+  for (int d = 1; d <= 4; ++d) {
+    double p = exp(-beta * (double)d);
+    thr[d] = (uint64_t)floor(ldexp(p, 32));
+  }
+  return 0;
+}
+
+/* ---------------------------------------------------------------------
+ * Counts straight from the definition (Eq. 1): each site's right and down
+ * bond, periodic, and the number of sites in each state (used by Eq. 7).
+ * ------------------------------------------------------------------- */
+void oracle_recount(const uint8_t *s, int32_t L, int32_t q, uint64_t *B,
+                    uint64_t *hist) {
+  uint64_t b = 0;
+  for (int32_t v = 0; v < q; ++v) hist[v] = 0;
+  for (int32_t i = 0; i < L; ++i) {
+    for (int32_t j = 0; j < L; ++j) {
+      uint8_t x = s[(int64_t)i * L + j];
+      uint8_t right = s[(int64_t)i * L + (j + 1) % L];
+      uint8_t down = s[(int64_t)((i + 1) % L) * L + j];
+      b += (x == right);
+      b += (x == down);
+      hist[x] += 1;
+    }
+  }
+  *B = b;
+}
+
+struct oracle_lattice {
+  int32_t L, q;
+  uint64_t seed;
+  uint64_t sweep;   /* global 0-based sweep index of the next sweep */
+  uint8_t *s;       /* L*L row-major */
+  uint64_t B;       /* satisfied bonds, kept incrementally */
+  uint64_t *hist;   /* q counters, kept incrementally */
+};
+
+static int32_t wrap(int32_t a, int32_t L) { return (a % L + L) % L; }
+
+/* Index of site (i,j) within its colour class: (i*L + j) / 2. */
+static uint64_t colour_index(int32_t L, int32_t i, int32_t j) {
+  return ((uint64_t)i * (uint64_t)L + (uint64_t)j) >> 1;
+}
+
+/* The single-site Metropolis rule.  `old` is the current spin, nb[0..3] its
+ * four neighbours, u the site's 32-bit random word.  Proposal
+ * s' = floor(u*q / 2^32) (uniform over all q states, the current one
+ * included); acceptance variate a = (u*q) mod 2^32; with H = -B the energy
+ * change is dE = n_old - n_new, where n_x counts the neighbours in state x;
+ * accept iff dE <= 0 or a < thr[dE].  Returns the new spin and stores the
+ * change of B in *dB. */
+static int metropolis_rule(int old, const int nb[4], uint32_t u, int32_t q,
+                           const uint64_t thr[5], int *dB) {
+  uint64_t prod = (uint64_t)u * (uint64_t)q;
+  int proposal = (int)(prod >> 32);
+  uint64_t a = (uint32_t)prod;
+  int n_old = 0, n_new = 0;
+  for (int n = 0; n < 4; ++n) {
+    n_old += nb[n] == old;
+    n_new += nb[n] == proposal;
+  }
+  int dE = n_old - n_new;
+  if ((dE <= 0) || (a < thr[dE])) {
+    *dB = n_new - n_old;
+    return proposal;
+  }
+  *dB = 0;
+  return old;
+}
+
+/* The four neighbours of (i,j) on the periodic lattice: up, down, left,
+ * right. */
+static void neighbours(const uint8_t *s, int32_t L, int32_t i, int32_t j,
+                       int nb[4]) {
+  nb[0] = s[(int64_t)wrap(i - 1, L) * L + j];
+  nb[1] = s[(int64_t)wrap(i + 1, L) * L + j];
+  nb[2] = s[(int64_t)i * L + wrap(j - 1, L)];
+  nb[3] = s[(int64_t)i * L + wrap(j + 1, L)];
+}
+
+/* One Metropolis trial at (i,j) during the pass of colour c of sweep t. */
+static int metropolis_site(const uint8_t *s, int32_t L, int32_t q,
+                           uint64_t seed, uint64_t t, int c,
+                           const uint64_t thr[5], int32_t i, int32_t j,
+                           int *dB) {
+  int nb[4];
+  neighbours(s, L, i, j, nb);
+  uint32_t u = oracle_site_word(seed, t, (uint32_t)c, colour_index(L, i, j));
+  return metropolis_rule(s[(int64_t)i * L + j], nb, u, q, thr, dB);
+}
+
+oracle_lattice *oracle_create(int32_t L, int32_t q, int32_t start,
+                              uint64_t seed) {
+  if (L < 3 || q < 2 || q > 256 || (start != 0 && start != 1)) return NULL;
+  if ((int64_t)L * L > ((int64_t)1 << 32)) return NULL;
+  oracle_lattice *lat = (oracle_lattice *)calloc(1, sizeof(*lat));
+  if (!lat) return NULL;
+  lat->L = L;
+  lat->q = q;
+  lat->seed = seed;
+  lat->sweep = 0;
+  lat->s = (uint8_t *)malloc((size_t)L * (size_t)L);
+  lat->hist = (uint64_t *)calloc((size_t)q, sizeof(uint64_t));
+  if (!lat->s || !lat->hist) {
+    oracle_destroy(lat);
+    return NULL;
+  }
+  for (int32_t i = 0; i < L; ++i) {
+    for (int32_t j = 0; j < L; ++j) {
+      uint8_t v = 0;
+      if (start == 1) {
+        /* Random start: i.i.d. uniform spins; the words of domain 2 + colour
+         * at sweep 0 give floor(u*q / 2^32). */
+        int c = (i + j) & 1;
+        uint32_t u =
+            oracle_site_word(seed, 0, 2u + (uint32_t)c, colour_index(L, i, j));
+        v = (uint8_t)(((uint64_t)u * (uint64_t)q) >> 32);
+      }
+      lat->s[(int64_t)i * L + j] = v;
+    }
+  }
+  oracle_recount(lat->s, L, q, &lat->B, lat->hist);
+  return lat;
+}
+
+void oracle_destroy(oracle_lattice *lat) {
+  if (!lat) return;
+  free(lat->s);
+  free(lat->hist);
+  free(lat);
+}
+
+int oracle_sweep(oracle_lattice *lat, double beta, int64_t nsweeps,
+                 uint64_t *out_counts, int32_t order, int32_t check) {
+  uint64_t thr[5];
+  if (!lat || nsweeps < 0 || (order != 0 && order != 1)) return -1;
+  if (oracle_thresholds(beta, thr) != 0) return -1;
+  const int32_t L = lat->L, q = lat->q;
+  uint64_t *tmp_hist = NULL;
+  if (check) {
+    tmp_hist = (uint64_t *)malloc((size_t)q * sizeof(uint64_t));
+    if (!tmp_hist) return -1;
+  }
+  for (int64_t n = 0; n < nsweeps; ++n) {
+    const uint64_t t = lat->sweep;
+    for (int c = 0; c < 2; ++c) {
+      for (int64_t r = 0; r < (int64_t)L * L; ++r) {
+        int64_t lin = order == 0 ? r : (int64_t)L * L - 1 - r;
+        int32_t i = (int32_t)(lin / L), j = (int32_t)(lin % L);
+        if (((i + j) & 1) != c) continue;
+        int dB = 0;
+        int old = lat->s[lin];
+        int now = metropolis_site(lat->s, L, q, lat->seed, t, c, thr, i, j,
+                                  &dB);
+        if (now != old) {
+          lat->hist[old] -= 1;
+          lat->hist[now] += 1;
+          lat->s[lin] = (uint8_t)now;
+        }
+        lat->B = (uint64_t)((int64_t)lat->B + dB);
+      }
+    }
+    lat->sweep = t + 1;
+    if (check) {
+      uint64_t b;
+      oracle_recount(lat->s, L, q, &b, tmp_hist);
+      if (b != lat->B ||
+          memcmp(tmp_hist, lat->hist, (size_t)q * sizeof(uint64_t)) != 0) {
+        free(tmp_hist);
+        return -2;
+      }
+    }
+    if (out_counts) {
+      uint64_t *rec = out_counts + n * (int64_t)(1 + q);
+      rec[0] = lat->B;
+      memcpy(rec + 1, lat->hist, (size_t)q * sizeof(uint64_t));
+    }
+  }
+  free(tmp_hist);
+  return 0;
+}
+
+void oracle_get_spins(const oracle_lattice *lat, uint8_t *out) {
+  memcpy(out, lat->s, (size_t)lat->L * (size_t)lat->L);
+}
+
+int oracle_set_state(oracle_lattice *lat, const uint8_t *spins,
+                     uint64_t sweep) {
+  for (int64_t n = 0; n < (int64_t)lat->L * lat->L; ++n)
+    if (spins[n] >= lat->q) return -1;
+  memcpy(lat->s, spins, (size_t)lat->L * (size_t)lat->L);
+  lat->sweep = sweep;
+  oracle_recount(lat->s, lat->L, lat->q, &lat->B, lat->hist);
+  return 0;
+}
+
+uint64_t oracle_sweep_index(const oracle_lattice *lat) { return lat->sweep; }
+
+void oracle_counts(const oracle_lattice *lat, uint64_t *B, uint64_t *hist) {
+  *B = lat->B;
+  memcpy(hist, lat->hist, (size_t)lat->q * sizeof(uint64_t));
+}
+
+/* A site's value after the white pass of sweep t: white sites take one
+ * Metropolis step against the pre-sweep black spins, black sites keep
+ * their value.  Valid for even L, where same-coloured sites never touch. */
+static int after_white(const uint8_t *pre, int32_t L, int32_t q,
+                       uint64_t seed, uint64_t t, const uint64_t thr[5],
+                       int32_t i, int32_t j) {
+  int dB;
+  if (((i + j) & 1) != 0) return pre[(int64_t)i * L + j];
+  return metropolis_site(pre, L, q, seed, t, 0, thr, i, j, &dB);
+}
+
+int oracle_sweep_sites(const uint8_t *pre, int32_t L, int32_t q,
+                       uint64_t seed, uint64_t sweep, double beta,
+                       int64_t nsites, const int64_t *idx, uint8_t *out) {
+  uint64_t thr[5];
+  if ((L & 1) != 0 || L < 4 || q < 2 || q > 256) return -1;
+  if (oracle_thresholds(beta, thr) != 0) return -1;
+  for (int64_t n = 0; n < nsites; ++n) {
+    int64_t lin = idx[n];
+    if (lin < 0 || lin >= (int64_t)L * L) return -1;
+    int32_t i = (int32_t)(lin / L), j = (int32_t)(lin % L);
+    if (((i + j) & 1) == 0) {
+      out[n] = (uint8_t)after_white(pre, L, q, seed, sweep, thr, i, j);
+      continue;
+    }
+    /* Black site: its four white neighbours as they are after the white
+     * pass, then one Metropolis step against them. */
+    int nb[4], dB;
+    const int32_t ni[4] = {wrap(i - 1, L), wrap(i + 1, L), i, i};
+    const int32_t nj[4] = {j, j, wrap(j - 1, L), wrap(j + 1, L)};
+    for (int m = 0; m < 4; ++m)
+      nb[m] = after_white(pre, L, q, seed, sweep, thr, ni[m], nj[m]);
+    uint32_t u = oracle_site_word(seed, sweep, 1u, colour_index(L, i, j));
+    out[n] = (uint8_t)metropolis_rule(pre[lin], nb, u, q, thr, &dB);
+  }
+  return 0;
+}
