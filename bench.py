@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""Benchmark of the checkerboard Metropolis sweep (one JSON line on rank 0).
+
+Workload (default): the paper-scale single lattice L = 32768 (1.07e9 spins,
+1 GiB of uint8 spins), q = 9, random start, seed 11, temperatures
+{0.995, 1.000, 1.005} T_c.  One step = one sweep (white pass, black pass
+fused with the per-sweep {B, hist} counts, record copied to the host,
+FP64 observables updated).  The timed steps are split evenly over the three
+temperatures, the spins carrying over (Sec. 3 protocol).
+
+Metric: ns per spin update (time / (N * sweeps)), whole job, lower is better.
+
+  value     device time (CUDA events on the library's stream) of the timed
+            sweeps, lattice resident in HBM (2 GiB of planes > 126 MB L2, so
+            no L2 flush is needed between steps).
+  e2e       the same sweeps issued one potts_sweep() call per step through
+            the public API, host buffers, wall clock: includes the launch, the
+            device->host copy of each step's record and the host-side FP64
+            observables.  beta travels by value in the launch (0 bytes H2D).
+  e2e_job   a whole job through the public API: upload of a host lattice
+            (pinned) with potts_set_state, the timed sweeps with records, and
+            potts_get_spins of the final lattice.
+  roofline  the colour-pass kernel against measured HBM bandwidth, 1.5 bytes
+            per spin per pass (read own plane, write own plane, read other
+            plane once) = 3 bytes per spin per sweep.
+  cpu_baseline  the serial CPU oracle on a bounded sample (one core).
+
+With torchrun (N > 1) each rank sweeps its own replica (weak scaling, no
+data-path collective); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ns/spin-update @L=32768 q=9 (frac HBM peak)"
+UNIT = "ns/update"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "colour_pass_L16384_q9.md")
+KERNEL_SOURCES = ["pass_u8.cuh", "philox.cuh", "kernels.cu"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1101_0876_gb300", "csrc", f),
+                  "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_per_launch(L: int):
+    """DRAM bytes per colour-pass launch from the committed ncu summary,
+    scaled from its lattice to L by the number of sites; None when the
+    kernel sources changed since the capture."""
+    try:
+        text = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    mh = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    mb = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    ml = re.search(r"capture_L:\s*(\d+)", text)
+    if not (mh and mb and ml) or mh.group(1) != kernel_hash():
+        return None
+    Lc = int(ml.group(1))
+    return float(mb.group(1)) * (L * L) / (Lc * Lc)
+
+
+# ------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}",
+                 f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, n in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(n)
+        pw = [float(r[3]) for r in self.rows
+              if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows),
+                "power_w_max": max(pw) if pw else None}
+
+
+# ------------------------------------------------------- distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def reduce_max(x: float, ws: int, device) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------ cpu baseline
+def cpu_oracle_ns_per_update(L: int, q: int, beta: float, sweeps: int,
+                             seed: int):
+    import oracle
+    lat = oracle.Lattice(L, q, 1, seed)
+    lat.sweep(beta, 1, records=False)            # warm caches
+    t0 = time.perf_counter()
+    lat.sweep(beta, sweeps)
+    dt = time.perf_counter() - t0
+    return dt * 1e9 / (L * L * sweeps), dt
+
+
+# --------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1101_0876_gb300 import potts, workloads
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    init_dist(ws, "nccl")
+    cfg = workloads.PAPER_Q9
+    L, q = args.L or cfg.L, cfg.q
+    N = L * L
+    seed = cfg.seed + rank          # each rank its own replica
+    temps = cfg.t_over_tc
+    betas = [workloads.beta_at(q, t) for t in temps]
+
+    stream = torch.cuda.Stream(device=dev)
+    lat = potts.Lattice(L, q, potts.START_RANDOM, seed)
+    lat.set_stream(stream.cuda_stream)
+
+    K, W = args.steps, args.warmup
+    seg = [K // 3 + (1 if k < K % 3 else 0) for k in range(3)]
+    recbuf = torch.empty((max(K, 1), 1 + q), dtype=torch.int64,
+                         pin_memory=True).numpy().view(np.uint64)
+
+    # warm-up (untimed)
+    lat.sweep(betas[0], W, records=False)
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+
+    # ---- device-timed region
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    off = 0
+    for b, n in zip(betas, seg):
+        lat.sweep(b, n, out=recbuf[off:off + n])
+        off += n
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    dev_ms = ev0.elapsed_time(ev1)
+    barrier(ws)
+    dev_ms_max = reduce_max(dev_ms, ws, dev)
+
+    # ---- end to end: one public-API call per step, host record buffers
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    step = 0
+    for b, n in zip(betas, seg):
+        for _ in range(n):
+            lat.sweep(b, 1, out=recbuf[step:step + 1])
+            step += 1
+    e2e_s = time.perf_counter() - t0
+    barrier(ws)
+    e2e_s_max = reduce_max(e2e_s, ws, dev)
+    clocks.stop()
+
+    # ---- whole job through the public API (upload, sweeps, download)
+    job = None
+    if not args.no_job:
+        host = torch.empty((L, L), dtype=torch.uint8,
+                           pin_memory=True).numpy()
+        host[:] = lat.spins()
+        out = torch.empty((L, L), dtype=torch.uint8, pin_memory=True).numpy()
+        barrier(ws)
+        t0 = time.perf_counter()
+        lat.set_state(host, 10**6)
+        off = 0
+        for b, n in zip(betas, seg):
+            lat.sweep(b, n, out=recbuf[off:off + n])
+            off += n
+        out[:] = lat.spins()
+        job_s = reduce_max(time.perf_counter() - t0, ws, dev)
+        job = {"value": job_s * 1e9 / (ws * N * K), "unit": UNIT,
+               "h2d_bytes_per_step": N / K, "d2h_bytes_per_step":
+               N / K + (1 + q) * 8, "note": "set_state upload + K sweeps + "
+               "get_spins download, amortised per step"}
+
+    if rank != 0:
+        return None
+
+    ns = dev_ms_max * 1e6 / (ws * N * K)
+    hbm, peak_kind = measured_peaks()
+    launches = 2 * K
+    pass_ms = dev_ms / launches
+    bytes_per_launch = 1.5 * N
+    achieved = bytes_per_launch / (pass_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC,
+        "value": ns,
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": dev_ms_max / K,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic (random start from Philox, seed 11 + rank)",
+        "config": {"workload": f"paper_scale_L{L}_q{q}_u8",
+                   "L": L, "q": q, "start": "random", "seed": cfg.seed,
+                   "t_over_tc": list(temps), "sweeps_per_step": 1,
+                   "l2": "no flush: 2 GiB of planes per sweep > 126 MB L2",
+                   "parallelism": f"replicas{ws}"},
+        "updates_per_s": ws * N * K / (dev_ms_max * 1e-3),
+        "e2e": {"value": e2e_s_max * 1e9 / (ws * N * K), "unit": UNIT,
+                "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": (1 + q) * 8},
+        "e2e_job": job,
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic_per_launch(L),
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "kernel": "colour pass (white; black fused with counts)",
+                     "bytes_per_launch": bytes_per_launch},
+        "clocks": clocks.summary(),
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        Lc, sweeps = args.cpu_L, args.cpu_sweeps
+        nsu, dt = cpu_oracle_ns_per_update(Lc, q, betas[1], sweeps, cfg.seed)
+        line["cpu_baseline"] = {
+            "value": nsu, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"serial oracle, L={Lc} q={q} random start at T_c, "
+                      f"{sweeps} sweeps ({dt:.1f} s); per-update cost of the "
+                      f"serial raster loop does not depend on L"}
+    return line
+
+
+# --------------------------------------------------- reference arm
+def run_reference(args):
+    """The CPU oracle as it stands, timed on the host cores, on the same
+    workload's metric: each step is one sweep of an L=cpu_L lattice (q=9,
+    random start, T around T_c); ns per update."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    from paper_1101_0876_gb300 import workloads
+    import oracle
+    cfg = workloads.PAPER_Q9
+    q = cfg.q
+    Lc = args.ref_L
+    betas = [workloads.beta_at(q, t) for t in cfg.t_over_tc]
+    lat = oracle.Lattice(Lc, q, 1, cfg.seed)
+    for k in range(args.warmup):
+        lat.sweep(betas[k % 3], 1, records=False)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        lat.sweep(betas[k % 3], 1)
+    dt = time.perf_counter() - t0
+    ns = dt * 1e9 / (Lc * Lc * args.steps)
+    sample = (f"serial oracle, L={Lc} q={q} random start, one sweep per "
+              f"step over T/T_c in {list(cfg.t_over_tc)}")
+    return {
+        "impl": "reference", "metric": METRIC, "value": ns, "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": {"workload": f"paper_scale_L{cfg.L}_q{q}_u8",
+                                        "sample_L": Lc},
+        "cpu_baseline": {"value": ns, "unit": UNIT, "cores": 1,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": ns, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=240)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=0, help="override lattice size")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-job", action="store_true")
+    ap.add_argument("--cpu-L", type=int, default=2048)
+    ap.add_argument("--cpu-sweeps", type=int, default=40)
+    ap.add_argument("--ref-L", type=int, default=1024)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    ws, _, _ = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * potts.h - C ABI of libpotts, a GB300 (sm_103a) implementation of the
+ * checkerboard Metropolis sweep of the two-dimensional ferromagnetic q-state
+ * Potts model, fused with per-sweep energy and magnetisation reductions.
+ *
+ * Method: Ferrero, De Francesco, Wolovick, Cannas, "q-state Potts model
+ * metastability study using optimized GPU-based Monte Carlo algorithms"
+ * (Comput. Phys. Commun. 2011, arXiv:1101.0876).
+ *   - Model: H = -J sum_<ij> delta(s_i, s_j), J = 1, k_B = 1, on the periodic
+ *     L x L square lattice (Sec. 2.1, Eq. 1).  Spins are 0..q-1 here (the
+ *     paper's 1..q shifted by -1).  The library reports B = -H, the number
+ *     of satisfied bonds, as an exact integer.
+ *   - Dynamics: Metropolis single-spin flips; a new state is proposed
+ *     uniformly among the q states and accepted with probability
+ *     min(1, exp(-beta dE)) (Sec. 2.2, Sec. 3.2).  One sweep (one MCS) is a
+ *     pass over all white sites ((i+j) even) followed by a pass over all
+ *     black sites (Sec. 3, "Red-Black Gauss-Seidel").
+ *   - Random numbers: counter-based Philox4x32-10 (Salmon et al., SC'11),
+ *     keyed by (seed, sweep, colour, site), replacing the paper's per-thread
+ *     multiply-with-carry generators (Sec. 3.2).  The word of colour-c site
+ *     k = (i*L + j) >> 1 in sweep t is word (k & 3) of
+ *     Philox(counter = (k >> 2, t mod 2^32, c, t >> 32),
+ *            key = (seed mod 2^32, seed >> 32)).
+ *     With u that word: proposal s' = floor(u q / 2^32); acceptance variate
+ *     a = (u q) mod 2^32; accept iff dE <= 0 or a < thr[dE] with
+ *     thr[d] = floor(2^32 exp(-beta d)) (the paper's table of Boltzmann
+ *     weights, Sec. 5).  Results therefore do not depend on how threads are
+ *     mapped to sites, and resuming from (spins, sweep) is exact.
+ *   - Counts: after every sweep the library forms the record
+ *     {B, hist[0..q-1]} (Sec. 3.4), from which e = -B/N and
+ *     m = (q N_max / N - 1)/(q - 1) (Eq. 7, read so that m = 1 when ordered
+ *     and 0 when disordered) are computed in FP64 on the host.
+ *
+ * Conventions for every function:
+ *   - Return value: POTTS_OK (0) or a positive POTTS_E* code.  No C++
+ *     exception and no abort crosses this boundary.  potts_last_error()
+ *     returns a message for the last failure on the calling thread.
+ *   - Ownership: the library owns all device memory behind a handle and
+ *     frees it in the matching destroy/stop call.  The caller owns every
+ *     buffer passed in (host memory unless stated otherwise).
+ *   - Threads: calls on one lattice or batch handle must not run
+ *     concurrently.  potts_serve_submit/poll/cancel are thread-safe.
+ *   - Streams: each handle runs on its own CUDA stream unless
+ *     potts_set_stream() gave it one; calls that return results to host
+ *     memory synchronise that stream before returning.
+ *   - Device: handles are bound to the device current at creation.
+ */
+#ifndef POTTS_H
+#define POTTS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  POTTS_OK = 0,
+  POTTS_EINVAL = 1,     /* bad argument (L, q, beta, pointer, layout...) */
+  POTTS_ENOMEM = 2,     /* device/host allocation failed or over budget */
+  POTTS_ECUDA = 3,      /* a CUDA runtime call failed (message kept) */
+  POTTS_ETIMEOUT = 4,   /* a bounded device or host wait gave up */
+  POTTS_EBUSY = 5,      /* server queue full (non-blocking submit) */
+  POTTS_ECANCELLED = 6, /* request was cancelled */
+  POTTS_ENOTFOUND = 7   /* unknown request id */
+};
+
+enum { POTTS_START_ORDERED = 0, POTTS_START_RANDOM = 1 };
+
+/* Spin storage in device memory.  U8: one byte per spin, two colour planes
+ * of L rows x L/2 bytes (the paper's byte-per-spin colour-packed layout,
+ * Sec. 3.3).  U4: two spins per byte (q <= 16), planes of L rows x L/4
+ * bytes.  AUTO picks U8. */
+enum { POTTS_LAYOUT_AUTO = 0, POTTS_LAYOUT_U8 = 1, POTTS_LAYOUT_U4 = 2 };
+
+typedef struct potts_lattice *potts_h;
+typedef struct potts_batch *potts_batch_h;
+typedef struct potts_server *potts_server_h;
+
+/* Message for the last failure on this thread ("" if none).  The pointer
+ * stays valid until the next failing call on the same thread. */
+const char *potts_last_error(void);
+
+/* Library version as an integer (major*10000 + minor*100 + patch). */
+int potts_version(void);
+
+/* ---------------------------------------------------------------- lattice
+ * potts_create: allocates an L x L lattice with q states on the current
+ * device and initialises it: ORDERED = every spin 0 (the paper's s_i = 1,
+ * Sec. 3 protocol); RANDOM = i.i.d. uniform spins drawn from the Philox
+ * words of domain 2 + colour at sweep 0 (s = floor(u q / 2^32)).
+ * Constraints: 32 <= L <= 65536, L % 32 == 0 (U4 needs L % 64 == 0);
+ * 2 <= q <= 256 (U4 needs q <= 16).  The sweep index starts at 0.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int potts_create(int32_t L, int32_t q, int32_t start, uint64_t seed,
+                 potts_h *out);
+int potts_create_ex(int32_t L, int32_t q, int32_t start, uint64_t seed,
+                    int32_t layout, potts_h *out);
+
+/* Runs nsweeps >= 0 sweeps at inverse temperature beta (finite, >= 0).
+ * out_counts: NULL, or host memory for nsweeps * (1 + q) uint64 laid out
+ * as one record {B, hist[0..q-1]} per sweep, in sweep order.  The running
+ * FP64 sums of potts_observables() are updated from every record.
+ * Returns after all sweeps finished.  Errors: EINVAL, ECUDA. */
+int potts_sweep(potts_h h, double beta, int64_t nsweeps,
+                uint64_t *out_counts);
+
+typedef struct {
+  uint64_t sweep;     /* sweeps done since create (= next sweep index) */
+  uint64_t bonds;     /* B of the last sweep (2N for a fresh ordered start) */
+  uint64_t nmax;      /* N_max = max_s hist[s] of the last sweep */
+  double e, m;        /* -B/N and (q N_max/N - 1)/(q - 1) of the last sweep */
+  uint64_t nsamples;  /* sweeps accumulated in the sums below */
+  double sum_e, sum_e2, sum_e4, sum_m, sum_m2;
+} potts_obs;
+
+/* Last-sweep values and running FP64 sums since create / reset. */
+int potts_observables(potts_h h, potts_obs *out);
+int potts_reset_averages(potts_h h);
+
+/* Copies the spins to host memory out_LxL (L*L bytes, row-major s[i*L+j]).
+ * Synchronises the handle's stream. */
+int potts_get_spins(potts_h h, uint8_t *out_LxL);
+
+/* Replaces the spins (host, L*L bytes row-major, each < q) and the sweep
+ * index; the next sweep uses index `sweep`.  B and the histogram are
+ * recounted.  Errors: EINVAL (a spin >= q), ECUDA. */
+int potts_set_state(potts_h h, const uint8_t *LxL, uint64_t sweep);
+
+/* The acceptance table used for beta: out_thr[d] = floor(2^32 exp(-beta d))
+ * for d = 1..4, out_thr[0] = 2^32, computed on the host in FP64.
+ * Errors: EINVAL for beta < 0 or not finite. */
+int potts_threshold_table(double beta, uint64_t out_thr[5]);
+
+/* Makes the handle run on `stream` (a cudaStream_t, or NULL for the
+ * handle's own stream).  The caller keeps ownership of the stream. */
+int potts_set_stream(potts_h h, void *stream);
+
+/* Device pointers of the two colour planes (white = 0, black = 1), their
+ * row pitch in bytes, and the layout, for callers that inspect the device
+ * state directly.  Read-only view; owned by the handle. */
+int potts_device_planes(potts_h h, void **white, void **black,
+                        int64_t *row_bytes, int32_t *layout);
+
+int potts_destroy(potts_h h);
+
+/* ------------------------------------------------------------------ batch
+ * n independent lattices (the paper's "several samples", Sec. 3) swept
+ * together: every colour pass of every lattice runs in one persistent
+ * launch over a flat (lattice, tile) work list, and k sweeps are captured in
+ * one CUDA graph.  Each lattice has its own L, q, start, seed, beta and
+ * sweep index; its results equal those of potts_create/potts_sweep with the
+ * same arguments bit for bit.
+ * Constraints per lattice as for potts_create (U8 layout).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int potts_batch_create(int32_t n, const int32_t *L, const int32_t *q,
+                       const int32_t *start, const uint64_t *seed,
+                       potts_batch_h *out);
+
+/* beta[n]; out_counts: NULL or an array of n host pointers, each NULL or
+ * room for nsweeps * (1 + q_i) uint64 records of lattice i. */
+int potts_batch_sweep(potts_batch_h b, const double *beta, int64_t nsweeps,
+                      uint64_t *const *out_counts);
+int potts_batch_get_spins(potts_batch_h b, int32_t i, uint8_t *out_LxL);
+int potts_batch_observables(potts_batch_h b, int32_t i, potts_obs *out);
+int potts_batch_destroy(potts_batch_h b);
+
+/* -------------------------------------------------------------- serving
+ * A request loop on a host thread with continuous batching: requests
+ * (L, q, beta, nsweeps, seed, start) are admitted while a slot is free and
+ * the device bytes in use plus the request's bytes fit the HBM budget; every
+ * step advances all active lattices by up to sweeps_per_step sweeps in one
+ * batched launch sequence; finished lattices free their slot and memory.
+ * Per-sweep records stream back through potts_serve_poll.  A request's
+ * records are identical to those of potts_create/potts_sweep with the same
+ * arguments, whatever else is running. */
+typedef struct {
+  uint64_t hbm_budget_bytes;  /* device bytes the server may hold */
+  int32_t max_slots;          /* lattices active at once */
+  int32_t sweeps_per_step;    /* sweeps per batched step (>= 1) */
+  int32_t queue_capacity;     /* pending requests before EBUSY (0 = 65536) */
+  int32_t reserved;
+} potts_serve_cfg;
+
+typedef struct {
+  int32_t L, q, start;
+  int32_t reserved;
+  double beta;
+  int64_t nsweeps;
+  uint64_t seed;
+} potts_req;
+
+typedef struct {
+  uint64_t submitted, admitted, completed, cancelled;
+  uint64_t steps, sweeps_done;    /* batched steps run, lattice-sweeps done */
+  uint64_t updates_done;          /* spin updates done (sum of L^2 per sweep) */
+  uint64_t bytes_in_use;          /* device bytes held by active lattices */
+  int32_t active, queued;
+} potts_serve_stats;
+
+int potts_serve_start(const potts_serve_cfg *cfg, potts_server_h *out);
+
+/* Enqueues a request; *req_id receives its id.  EBUSY if the queue is full,
+ * EINVAL if the request can never be admitted (bad arguments or larger than
+ * the budget). */
+int potts_serve_submit(potts_server_h s, const potts_req *req,
+                       uint64_t *req_id);
+
+/* Copies up to max_sweeps new records of the request (oldest first) to
+ * out_counts (room for max_sweeps * (1 + q) uint64), sets *n_ready to the
+ * number copied and *done to 1 once every record of a finished request has
+ * been returned (the request is then forgotten).  Never blocks.
+ * Errors: ENOTFOUND, ECANCELLED (cancelled request; *done = 1). */
+int potts_serve_poll(potts_server_h s, uint64_t req_id, uint64_t *out_counts,
+                     int64_t max_sweeps, int64_t *n_ready, int *done);
+
+/* Cancels a queued or running request; its slot and memory are freed at the
+ * next step boundary. */
+int potts_serve_cancel(potts_server_h s, uint64_t req_id);
+
+int potts_serve_stats_get(potts_server_h s, potts_serve_stats *out);
+
+/* Stops the loop: running requests are cancelled, all memory is freed. */
+int potts_serve_stop(potts_server_h s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POTTS_H */

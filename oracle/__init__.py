@@ -80,6 +80,10 @@ def lib() -> ctypes.CDLL:
                                          ctypes.c_double, ctypes.c_int64,
                                          i64p, u8p]
         L.oracle_sweep_sites.restype = ctypes.c_int
+        L.oracle_init_sites.argtypes = [ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_uint64,
+                                        ctypes.c_int64, i64p, u8p]
+        L.oracle_init_sites.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -137,6 +141,19 @@ def sweep_sites(pre: np.ndarray, q: int, seed: int, sweep: int, beta: float,
                                   _ptr(out, ctypes.c_uint8))
     if rc != 0:
         raise ValueError("oracle_sweep_sites: bad arguments")
+    return out
+
+
+def init_sites(L: int, q: int, start: int, seed: int,
+               idx: np.ndarray) -> np.ndarray:
+    """Initial spins of the sites idx (= i*L + j)."""
+    ix = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros(ix.size, dtype=np.uint8)
+    rc = lib().oracle_init_sites(L, q, start, seed, ix.size,
+                                 _ptr(ix, ctypes.c_int64),
+                                 _ptr(out, ctypes.c_uint8))
+    if rc != 0:
+        raise ValueError("oracle_init_sites: bad arguments")
     return out
 
 

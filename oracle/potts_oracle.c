@@ -173,6 +173,28 @@ static int metropolis_site(const uint8_t *s, int32_t L, int32_t q,
   return metropolis_rule(s[(int64_t)i * L + j], nb, u, q, thr, dB);
 }
 
+/* Initial spin of site (i,j).  Ordered start: 0 (the paper's s_i = 1,
+ * Sec. 3 protocol).  Random start: i.i.d. uniform, floor(u*q / 2^32) with u
+ * the site's word of domain 2 + colour at sweep 0. */
+static uint8_t initial_spin(int32_t L, int32_t q, int32_t start, uint64_t seed,
+                            int32_t i, int32_t j) {
+  if (start == 0) return 0;
+  int c = (i + j) & 1;
+  uint32_t u = oracle_site_word(seed, 0, 2u + (uint32_t)c, colour_index(L, i, j));
+  return (uint8_t)(((uint64_t)u * (uint64_t)q) >> 32);
+}
+
+int oracle_init_sites(int32_t L, int32_t q, int32_t start, uint64_t seed,
+                      int64_t nsites, const int64_t *idx, uint8_t *out) {
+  if (L < 3 || q < 2 || q > 256 || (start != 0 && start != 1)) return -1;
+  for (int64_t n = 0; n < nsites; ++n) {
+    if (idx[n] < 0 || idx[n] >= (int64_t)L * L) return -1;
+    out[n] = initial_spin(L, q, start, seed, (int32_t)(idx[n] / L),
+                          (int32_t)(idx[n] % L));
+  }
+  return 0;
+}
+
 oracle_lattice *oracle_create(int32_t L, int32_t q, int32_t start,
                               uint64_t seed) {
   if (L < 3 || q < 2 || q > 256 || (start != 0 && start != 1)) return NULL;
@@ -189,20 +211,9 @@ oracle_lattice *oracle_create(int32_t L, int32_t q, int32_t start,
     oracle_destroy(lat);
     return NULL;
   }
-  for (int32_t i = 0; i < L; ++i) {
-    for (int32_t j = 0; j < L; ++j) {
-      uint8_t v = 0;
-      if (start == 1) {
-        /* Random start: i.i.d. uniform spins; the words of domain 2 + colour
-         * at sweep 0 give floor(u*q / 2^32). */
-        int c = (i + j) & 1;
-        uint32_t u =
-            oracle_site_word(seed, 0, 2u + (uint32_t)c, colour_index(L, i, j));
-        v = (uint8_t)(((uint64_t)u * (uint64_t)q) >> 32);
-      }
-      lat->s[(int64_t)i * L + j] = v;
-    }
-  }
+  for (int32_t i = 0; i < L; ++i)
+    for (int32_t j = 0; j < L; ++j)
+      lat->s[(int64_t)i * L + j] = initial_spin(L, q, start, seed, i, j);
   oracle_recount(lat->s, L, q, &lat->B, lat->hist);
   return lat;
 }

@@ -43,6 +43,10 @@ int oracle_thresholds(double beta, uint64_t thr[5]);
 void oracle_recount(const uint8_t *s, int32_t L, int32_t q, uint64_t *B,
                     uint64_t *hist);
 
+/* Initial spins of the sites idx[n] (= i*L + j) for the given start. */
+int oracle_init_sites(int32_t L, int32_t q, int32_t start, uint64_t seed,
+                      int64_t nsites, const int64_t *idx, uint8_t *out);
+
 /* Opaque lattice state. */
 typedef struct oracle_lattice oracle_lattice;
 

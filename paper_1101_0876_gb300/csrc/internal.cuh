@@ -1,0 +1,74 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <string>
+
+#include "../../include/potts.h"
+#include "pass_u8.cuh"
+
+namespace potts {
+
+// ------------------------------------------------------------- errors
+int fail(int code, const char *fmt, ...);
+void clear_error();
+
+#define POTTS_CK(call)                                                     \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess)                                                 \
+      return ::potts::fail(POTTS_ECUDA, "%s failed: %s (%s:%d)", #call,    \
+                           cudaGetErrorString(e_), __FILE__, __LINE__);    \
+  } while (0)
+
+// ---------------------------------------------------------- geometry
+// CTA work shape of a colour pass: CX 16-byte chunks per CTA row, RG row
+// groups per CTA, each thread walking TR rows.  128 threads per CTA.
+struct TileGeom {
+  int32_t CX, RG, TR;
+  int32_t gx, gy;  // grid
+};
+constexpr int kPassThreads = 128;
+
+TileGeom choose_geom(int32_t L, int32_t H, int32_t sm_count, int32_t tr_hint);
+
+// Spin-width class: every spin < 2^qbits.
+int qbits_for(int32_t q);
+
+// Threshold table from beta (host FP64, glibc exp):
+// thr[d] = floor(2^32 exp(-beta d)), thr[0] = 2^32.
+bool threshold_table(double beta, uint64_t thr[5]);
+AcceptTable accept_table(const uint64_t thr[5]);
+
+// ----------------------------------------------------------- launches
+// One colour pass of one lattice.  rec != nullptr only on the black pass:
+// it receives {B, hist[q]} (added atomically; must start at zero).
+cudaError_t launch_pass(const PassArgs &A, const AcceptTable &T,
+                        const TileGeom &G, unsigned long long *rec,
+                        cudaStream_t st);
+// Random start of one plane: s = floor(u q / 2^32), u = Philox word of
+// domain 2 + colour at sweep 0.
+cudaError_t launch_init_random(uint8_t *plane, int64_t plane_bytes, uint32_t q,
+                               uint32_t colour, uint64_t seed,
+                               cudaStream_t st);
+// Recount {B, hist} from the planes into rec (must start at zero).
+cudaError_t launch_recount(const uint8_t *white, const uint8_t *black,
+                           int32_t L, int32_t H, uint32_t q,
+                           unsigned long long *rec, cudaStream_t st);
+
+int sm_count_of_current_device();
+
+// FP64 observables of one record.
+void update_obs(potts_obs *obs, const uint64_t *rec, int32_t L, int32_t q,
+                bool accumulate);
+
+// Host-side (de)interleaving between the row-major L x L layout and the two
+// colour planes (L rows x H bytes each).
+void planes_to_rowmajor(const uint8_t *white, const uint8_t *black, int32_t L,
+                        uint8_t *out);
+void rowmajor_to_planes(const uint8_t *in, int32_t L, uint8_t *white,
+                        uint8_t *black);
+
+}  // namespace potts

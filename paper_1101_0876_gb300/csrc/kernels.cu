@@ -1,0 +1,226 @@
+// Kernels of the single-lattice path: the colour pass (white pass, and the
+// black pass fused with the per-sweep counts), the random start and a full
+// recount.  The per-thread work is in pass_u8.cuh.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace potts {
+
+// ------------------------------------------------------------ the pass
+// Grid: (gx, gy) CTAs of 128 threads.  Thread t of CTA (bx, by) owns chunk
+// bx*CX + t%CX (16 bytes) and rows starting at (by*RG + t/CX)*TR.
+// COUNTS (black pass): after the walk, the satisfied-bond count of the
+// updated sites and the per-lane shared histogram are reduced (warp shuffle,
+// shared atomics) and added with one 64-bit atomic per CTA for B and one per
+// non-empty state for the histogram (Sec. 3.4: per-block energies and state
+// counters, summed; here without a second kernel or a CPU-side sum).
+template <int QB, bool COUNTS, bool LT0>
+__global__ void __launch_bounds__(kPassThreads)
+    pass_kernel(PassArgs A, AcceptTable Tin, TileGeom G,
+                unsigned long long *rec) {
+  extern __shared__ uint32_t s_hist[];  // q * 32 counters (COUNTS only)
+  __shared__ uint32_t s_tab[9];
+  __shared__ uint32_t s_sat;
+  const uint32_t tid = threadIdx.x;
+  if (tid < 9) s_tab[tid] = Tin.tab[tid];
+  if (COUNTS) {
+    for (uint32_t v = tid; v < A.q * 32u; v += kPassThreads) s_hist[v] = 0;
+    if (tid == 0) s_sat = 0;
+  }
+  __syncthreads();
+
+  const PhiloxKey ks = philox_schedule(A.key0, A.key1);
+  const int32_t cx = (int32_t)tid % G.CX, rg = (int32_t)tid / G.CX;
+  const int32_t chunk = (int32_t)blockIdx.x * G.CX + cx;
+  const int32_t i0 = ((int32_t)blockIdx.y * G.RG + rg) * G.TR;
+  uint32_t ne = 0;
+  int32_t rows = 0;
+  if (rg < G.RG && chunk * 16 < A.H && i0 < A.L) {
+    rows = min(G.TR, A.L - i0);
+    walk_column<QB, COUNTS, LT0>(A, ks, s_tab, chunk * 16, i0, rows, s_hist,
+                                 tid & 31u, &ne);
+  }
+  if (COUNTS) {
+    uint32_t sat = 64u * (uint32_t)rows - ne;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sat += __shfl_xor_sync(0xFFFFFFFFu, sat, o);
+    if ((tid & 31u) == 0 && sat) atomicAdd(&s_sat, sat);
+    __syncthreads();
+    if (tid == 0 && s_sat) atomicAdd(rec, (unsigned long long)s_sat);
+    for (uint32_t v = tid; v < A.q; v += kPassThreads) {
+      uint32_t sum = 0;
+#pragma unroll 8
+      for (int l = 0; l < 32; ++l) sum += s_hist[v * 32u + l];
+      if (sum) atomicAdd(rec + 1 + v, (unsigned long long)sum);
+    }
+  }
+}
+
+template <int QB>
+static cudaError_t launch_qb(const PassArgs &A, const AcceptTable &T,
+                             const TileGeom &G, unsigned long long *rec,
+                             cudaStream_t st) {
+  dim3 grid(G.gx, G.gy), block(kPassThreads);
+  if (rec) {
+    const size_t smem = (size_t)A.q * 32u * sizeof(uint32_t);
+    if (T.rule_lt0)
+      pass_kernel<QB, true, true><<<grid, block, smem, st>>>(A, T, G, rec);
+    else
+      pass_kernel<QB, true, false><<<grid, block, smem, st>>>(A, T, G, rec);
+  } else {
+    if (T.rule_lt0)
+      pass_kernel<QB, false, true><<<grid, block, 0, st>>>(A, T, G, nullptr);
+    else
+      pass_kernel<QB, false, false><<<grid, block, 0, st>>>(A, T, G, nullptr);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass(const PassArgs &A, const AcceptTable &T,
+                        const TileGeom &G, unsigned long long *rec,
+                        cudaStream_t st) {
+  switch (qbits_for((int32_t)A.q)) {
+    case 4: return launch_qb<4>(A, T, G, rec, st);
+    case 5: return launch_qb<5>(A, T, G, rec, st);
+    case 6: return launch_qb<6>(A, T, G, rec, st);
+    case 7: return launch_qb<7>(A, T, G, rec, st);
+    default: return launch_qb<8>(A, T, G, rec, st);
+  }
+}
+
+int qbits_for(int32_t q) {
+  if (q <= 16) return 4;
+  if (q <= 32) return 5;
+  if (q <= 64) return 6;
+  if (q <= 128) return 7;
+  return 8;
+}
+
+TileGeom choose_geom(int32_t L, int32_t H, int32_t sm_count,
+                     int32_t tr_hint) {
+  TileGeom g;
+  const int32_t nchunks = H / 16;
+  g.CX = std::min(nchunks, kPassThreads);
+  g.RG = kPassThreads / g.CX;
+  // Aim for a few waves of 16 resident CTAs per SM before lengthening walks.
+  const int64_t walkers = (int64_t)nchunks * L;
+  const int64_t target = (int64_t)std::max(sm_count, 1) * 2048 * 2;
+  int32_t tr = 1;
+  if (tr_hint > 0) {
+    tr = tr_hint;
+  } else {
+    while (tr < 32 && walkers / (2 * tr) >= target) tr *= 2;
+  }
+  g.TR = std::min(tr, L);
+  g.gx = (nchunks + g.CX - 1) / g.CX;
+  const int32_t rows_per_cta = g.RG * g.TR;
+  g.gy = (L + rows_per_cta - 1) / rows_per_cta;
+  return g;
+}
+
+// -------------------------------------------------------- random start
+__global__ void init_random_kernel(uint8_t *plane, int64_t nchunks,
+                                   uint32_t q, uint32_t domain, uint32_t key0,
+                                   uint32_t key1) {
+  const PhiloxKey ks = philox_schedule(key0, key1);
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint4 u = philox10((uint32_t)(c * 4 + j), 0u, domain, 0u, ks);
+      const uint32_t p0 = (uint32_t)(((uint64_t)u.x * q) >> 32);
+      const uint32_t p1 = (uint32_t)(((uint64_t)u.y * q) >> 32);
+      const uint32_t p2 = (uint32_t)(((uint64_t)u.z * q) >> 32);
+      const uint32_t p3 = (uint32_t)(((uint64_t)u.w * q) >> 32);
+      w[j] = pack4(p0, p1, p2, p3);
+    }
+    reinterpret_cast<uint4 *>(plane)[c] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+cudaError_t launch_init_random(uint8_t *plane, int64_t plane_bytes, uint32_t q,
+                               uint32_t colour, uint64_t seed,
+                               cudaStream_t st) {
+  const int64_t nchunks = plane_bytes / 16;
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>((nchunks + threads - 1) / threads,
+                                           (int64_t)1 << 20);
+  init_random_kernel<<<(unsigned)blocks, threads, 0, st>>>(
+      plane, nchunks, q, 2u + colour, (uint32_t)seed, (uint32_t)(seed >> 32));
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ recount
+// One thread per 16-byte chunk of a black row: satisfied bonds of the 16
+// black sites with their four white neighbours, and the states of those
+// black sites and of the white sites at the same (i, x).
+__global__ void recount_kernel(const uint8_t *white, const uint8_t *black,
+                               int32_t L, int32_t H, uint32_t q,
+                               unsigned long long *rec) {
+  extern __shared__ uint32_t s_hist[];
+  __shared__ uint32_t s_sat;
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t v = tid; v < q * 32u; v += blockDim.x) s_hist[v] = 0;
+  if (tid == 0) s_sat = 0;
+  __syncthreads();
+  const int64_t nch = (int64_t)L * (H / 16);
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + tid;
+  uint32_t sat = 0;
+  if (c < nch) {
+    const int32_t i = (int32_t)(c / (H / 16));
+    const int32_t x0 = (int32_t)(c % (H / 16)) * 16;
+    const int32_t im = i == 0 ? L - 1 : i - 1, ip = i + 1 == L ? 0 : i + 1;
+    const uint4 U = *reinterpret_cast<const uint4 *>(white + (int64_t)im * H + x0);
+    const uint4 D = *reinterpret_cast<const uint4 *>(white + (int64_t)ip * H + x0);
+    const uint4 C = *reinterpret_cast<const uint4 *>(white + (int64_t)i * H + x0);
+    const uint4 S = *reinterpret_cast<const uint4 *>(black + (int64_t)i * H + x0);
+    const bool left = ((i + 1) & 1) == 0;  // black: x-1 when i+1 even
+    const int32_t xe = left ? (x0 == 0 ? H - 4 : x0 - 4) : (x0 + 16 == H ? 0 : x0 + 16);
+    const uint32_t ew = *reinterpret_cast<const uint32_t *>(white + (int64_t)i * H + xe);
+    const uint32_t Cw[4] = {C.x, C.y, C.z, C.w};
+    const uint32_t Uw[4] = {U.x, U.y, U.z, U.w};
+    const uint32_t Dw[4] = {D.x, D.y, D.z, D.w};
+    const uint32_t Sw[4] = {S.x, S.y, S.z, S.w};
+    uint32_t Wd[4];
+    if (left) {
+      Wd[0] = __funnelshift_l(ew, Cw[0], 8);
+      for (int k = 1; k < 4; ++k) Wd[k] = __funnelshift_l(Cw[k - 1], Cw[k], 8);
+    } else {
+      for (int k = 0; k < 3; ++k) Wd[k] = __funnelshift_r(Cw[k], Cw[k + 1], 8);
+      Wd[3] = __funnelshift_r(Cw[3], ew, 8);
+    }
+    uint32_t ne = 0;
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t n16 = ne16_sum4<8>(Sw[k] ^ Uw[k], Sw[k] ^ Dw[k],
+                                        Sw[k] ^ Cw[k], Sw[k] ^ Wd[k]);
+      ne += ((n16 >> 4) * 0x01010101u) >> 24;
+      hist_word(s_hist, tid & 31u, Sw[k]);
+      hist_word(s_hist, tid & 31u, Cw[k]);
+    }
+    sat = 64u - ne;
+  }
+  for (int o = 16; o > 0; o >>= 1) sat += __shfl_xor_sync(0xFFFFFFFFu, sat, o);
+  if ((tid & 31u) == 0 && sat) atomicAdd(&s_sat, sat);
+  __syncthreads();
+  if (tid == 0 && s_sat) atomicAdd(rec, (unsigned long long)s_sat);
+  for (uint32_t v = tid; v < q; v += blockDim.x) {
+    uint32_t sum = 0;
+    for (int l = 0; l < 32; ++l) sum += s_hist[v * 32u + l];
+    if (sum) atomicAdd(rec + 1 + v, (unsigned long long)sum);
+  }
+}
+
+cudaError_t launch_recount(const uint8_t *white, const uint8_t *black,
+                           int32_t L, int32_t H, uint32_t q,
+                           unsigned long long *rec, cudaStream_t st) {
+  const int64_t nch = (int64_t)L * (H / 16);
+  const int threads = 256;
+  const int64_t blocks = (nch + threads - 1) / threads;
+  recount_kernel<<<(unsigned)blocks, threads, (size_t)q * 32u * 4u, st>>>(
+      white, black, L, H, q, rec);
+  return cudaGetLastError();
+}
+
+}  // namespace potts

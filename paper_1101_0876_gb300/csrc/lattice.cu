@@ -1,0 +1,367 @@
+// C ABI of the single-lattice path: create / sweep / observables / state.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace potts {
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+void clear_error() { g_err.clear(); }
+
+int sm_count_of_current_device() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+      cudaSuccess)
+    return 1;
+  return n;
+}
+
+// ------------------------------------------------------- threshold table
+// Sec. 5 (CPU code): a table of Boltzmann weights per temperature.  Here the
+// weight exp(-beta d) of an energy increase d = 1..4 becomes the 32-bit
+// fixed-point threshold floor(2^32 exp(-beta d)), computed on the host in
+// FP64 with the C library's exp.
+bool threshold_table(double beta, uint64_t thr[5]) {
+  if (!(beta >= 0.0) || !std::isfinite(beta)) return false;
+  thr[0] = (uint64_t)1 << 32;
+  for (int d = 1; d <= 4; ++d) {
+    const double w = std::exp(-beta * (double)d);
+    thr[d] = (uint64_t)std::floor(std::ldexp(w, 32));
+  }
+  return true;
+}
+
+AcceptTable accept_table(const uint64_t thr[5]) {
+  AcceptTable T;
+  bool any_zero = false;
+  for (int d = 1; d <= 4; ++d) any_zero |= thr[d] == 0;
+  T.rule_lt0 = any_zero ? 1u : 0u;
+  for (int i = 0; i < 9; ++i) {
+    const int dE = i - 4;
+    if (any_zero) {
+      // accept iff dE <= 0 or a < thr[dE]
+      T.tab[i] = dE <= 0 ? 0xFFFFFFFFu
+                         : (uint32_t)std::min<uint64_t>(thr[dE], 0xFFFFFFFFu);
+    } else {
+      // accept iff a <= thr[dE] - 1  (thr[dE] in [1, 2^32])
+      T.tab[i] = dE <= 0 ? 0xFFFFFFFFu : (uint32_t)(thr[dE] - 1);
+    }
+  }
+  return T;
+}
+
+// ---------------------------------------------------------- observables
+void update_obs(potts_obs *obs, const uint64_t *rec, int32_t L, int32_t q,
+                bool accumulate) {
+  const double N = (double)L * (double)L;
+  uint64_t nmax = 0;
+  for (int v = 0; v < q; ++v) nmax = std::max(nmax, rec[1 + v]);
+  obs->bonds = rec[0];
+  obs->nmax = nmax;
+  obs->e = -(double)rec[0] / N;
+  obs->m = ((double)q * (double)nmax / N - 1.0) / ((double)q - 1.0);
+  if (accumulate) {
+    const double e = obs->e, m = obs->m, e2 = e * e;
+    obs->nsamples += 1;
+    obs->sum_e += e;
+    obs->sum_e2 += e2;
+    obs->sum_e4 += e2 * e2;
+    obs->sum_m += m;
+    obs->sum_m2 += m * m;
+  }
+}
+
+void planes_to_rowmajor(const uint8_t *white, const uint8_t *black, int32_t L,
+                        uint8_t *out) {
+  const int64_t H = L / 2;
+  for (int64_t i = 0; i < L; ++i) {
+    const uint8_t *w = white + i * H, *b = black + i * H;
+    uint8_t *o = out + i * L;
+    if ((i & 1) == 0) {
+      for (int64_t x = 0; x < H; ++x) { o[2 * x] = w[x]; o[2 * x + 1] = b[x]; }
+    } else {
+      for (int64_t x = 0; x < H; ++x) { o[2 * x] = b[x]; o[2 * x + 1] = w[x]; }
+    }
+  }
+}
+
+void rowmajor_to_planes(const uint8_t *in, int32_t L, uint8_t *white,
+                        uint8_t *black) {
+  const int64_t H = L / 2;
+  for (int64_t i = 0; i < L; ++i) {
+    uint8_t *w = white + i * H, *b = black + i * H;
+    const uint8_t *s = in + i * L;
+    if ((i & 1) == 0) {
+      for (int64_t x = 0; x < H; ++x) { w[x] = s[2 * x]; b[x] = s[2 * x + 1]; }
+    } else {
+      for (int64_t x = 0; x < H; ++x) { b[x] = s[2 * x]; w[x] = s[2 * x + 1]; }
+    }
+  }
+}
+
+}  // namespace potts
+
+using namespace potts;
+
+struct potts_lattice {
+  int32_t L = 0, q = 0, layout = POTTS_LAYOUT_U8;
+  int32_t H = 0;            // bytes per plane row
+  uint64_t seed = 0;
+  uint64_t sweep = 0;       // next global sweep index
+  int device = 0;
+  uint8_t *d_planes = nullptr;  // white plane then black plane
+  int64_t plane_bytes = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  unsigned long long *d_rec = nullptr;  // [rec_cap][1+q]
+  uint64_t *h_rec = nullptr;            // pinned copy
+  int64_t rec_cap = 0;
+  TileGeom geom{};
+  potts_obs obs{};
+};
+
+static constexpr int64_t kRecordBytesTarget = 4 << 20;
+
+static int recount_into_obs(potts_h h) {
+  const int32_t q = h->q;
+  POTTS_CK(cudaMemsetAsync(h->d_rec, 0, (size_t)(1 + q) * 8, h->stream));
+  POTTS_CK(launch_recount(h->d_planes, h->d_planes + h->plane_bytes, h->L,
+                          h->H, (uint32_t)q, h->d_rec, h->stream));
+  POTTS_CK(cudaMemcpyAsync(h->h_rec, h->d_rec, (size_t)(1 + q) * 8,
+                           cudaMemcpyDeviceToHost, h->stream));
+  POTTS_CK(cudaStreamSynchronize(h->stream));
+  update_obs(&h->obs, h->h_rec, h->L, q, false);
+  return POTTS_OK;
+}
+
+static void free_lattice(potts_h h) {
+  if (!h) return;
+  if (h->d_planes) cudaFree(h->d_planes);
+  if (h->d_rec) cudaFree(h->d_rec);
+  if (h->h_rec) cudaFreeHost(h->h_rec);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  delete h;
+}
+
+extern "C" {
+
+const char *potts_last_error(void) { return g_err.c_str(); }
+
+int potts_version(void) { return 100; }
+
+int potts_threshold_table(double beta, uint64_t out_thr[5]) {
+  if (!out_thr) return fail(POTTS_EINVAL, "out_thr is NULL");
+  if (!threshold_table(beta, out_thr))
+    return fail(POTTS_EINVAL, "beta must be finite and >= 0 (got %g)", beta);
+  return POTTS_OK;
+}
+
+int potts_create_ex(int32_t L, int32_t q, int32_t start, uint64_t seed,
+                    int32_t layout, potts_h *out) {
+  if (!out) return fail(POTTS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (layout == POTTS_LAYOUT_AUTO) layout = POTTS_LAYOUT_U8;
+  if (layout != POTTS_LAYOUT_U8)
+    return fail(POTTS_EINVAL, "layout %d is not available", layout);
+  if (L < 32 || L > 65536 || L % 32 != 0)
+    return fail(POTTS_EINVAL, "L must be a multiple of 32 in [32, 65536] (got %d)", L);
+  if (q < 2 || q > 256) return fail(POTTS_EINVAL, "q must be in [2, 256] (got %d)", q);
+  if (start != POTTS_START_ORDERED && start != POTTS_START_RANDOM)
+    return fail(POTTS_EINVAL, "start must be 0 (ordered) or 1 (random)");
+  potts_h h = new (std::nothrow) potts_lattice();
+  if (!h) return fail(POTTS_ENOMEM, "host allocation failed");
+  h->L = L;
+  h->q = q;
+  h->H = L / 2;
+  h->layout = layout;
+  h->seed = seed;
+  h->plane_bytes = (int64_t)L * (L / 2);
+  int rc = POTTS_OK;
+  do {
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) { rc = fail(POTTS_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e)); break; }
+    e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { rc = fail(POTTS_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)); break; }
+    h->stream = h->own_stream;
+    e = cudaMalloc(&h->d_planes, (size_t)(2 * h->plane_bytes));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      h->d_planes = nullptr;
+      rc = fail(POTTS_ENOMEM, "cudaMalloc(%lld bytes) for the planes: %s",
+                (long long)(2 * h->plane_bytes), cudaGetErrorString(e));
+      break;
+    }
+    h->rec_cap = std::max<int64_t>(1, kRecordBytesTarget / ((1 + q) * 8));
+    const size_t rec_bytes = (size_t)h->rec_cap * (1 + q) * 8;
+    e = cudaMalloc(&h->d_rec, rec_bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); h->d_rec = nullptr; rc = fail(POTTS_ENOMEM, "cudaMalloc records: %s", cudaGetErrorString(e)); break; }
+    e = cudaMallocHost(&h->h_rec, rec_bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); h->h_rec = nullptr; rc = fail(POTTS_ENOMEM, "cudaMallocHost records: %s", cudaGetErrorString(e)); break; }
+    h->geom = choose_geom(L, h->H, sm_count_of_current_device(), 0);
+    if (start == POTTS_START_ORDERED) {
+      e = cudaMemsetAsync(h->d_planes, 0, (size_t)(2 * h->plane_bytes), h->stream);
+    } else {
+      e = launch_init_random(h->d_planes, h->plane_bytes, (uint32_t)q, 0, seed, h->stream);
+      if (e == cudaSuccess)
+        e = launch_init_random(h->d_planes + h->plane_bytes, h->plane_bytes, (uint32_t)q, 1, seed, h->stream);
+    }
+    if (e != cudaSuccess) { rc = fail(POTTS_ECUDA, "init: %s", cudaGetErrorString(e)); break; }
+    rc = recount_into_obs(h);
+  } while (0);
+  if (rc != POTTS_OK) {
+    free_lattice(h);
+    return rc;
+  }
+  *out = h;
+  clear_error();
+  return POTTS_OK;
+}
+
+int potts_create(int32_t L, int32_t q, int32_t start, uint64_t seed,
+                 potts_h *out) {
+  return potts_create_ex(L, q, start, seed, POTTS_LAYOUT_AUTO, out);
+}
+
+int potts_sweep(potts_h h, double beta, int64_t nsweeps, uint64_t *out_counts) {
+  if (!h) return fail(POTTS_EINVAL, "handle is NULL");
+  if (nsweeps < 0) return fail(POTTS_EINVAL, "nsweeps < 0");
+  uint64_t thr[5];
+  if (!threshold_table(beta, thr))
+    return fail(POTTS_EINVAL, "beta must be finite and >= 0 (got %g)", beta);
+  const AcceptTable T = accept_table(thr);
+  const int32_t q = h->q;
+  const int64_t rec_len = 1 + q;
+  PassArgs A[2];
+  for (int c = 0; c < 2; ++c) {
+    A[c].own = h->d_planes + (c ? h->plane_bytes : 0);
+    A[c].other = h->d_planes + (c ? 0 : h->plane_bytes);
+    A[c].L = h->L;
+    A[c].H = h->H;
+    A[c].q = (uint32_t)q;
+    A[c].colour = (uint32_t)c;
+    A[c].key0 = (uint32_t)h->seed;
+    A[c].key1 = (uint32_t)(h->seed >> 32);
+  }
+  int64_t done = 0;
+  while (done < nsweeps) {
+    const int64_t n = std::min(nsweeps - done, h->rec_cap);
+    POTTS_CK(cudaMemsetAsync(h->d_rec, 0, (size_t)(n * rec_len * 8), h->stream));
+    for (int64_t s = 0; s < n; ++s) {
+      const uint64_t t = h->sweep + (uint64_t)s;
+      for (int c = 0; c < 2; ++c) {
+        A[c].t_lo = (uint32_t)t;
+        A[c].t_hi = (uint32_t)(t >> 32);
+        POTTS_CK(launch_pass(A[c], T, h->geom,
+                             c ? h->d_rec + s * rec_len : nullptr, h->stream));
+      }
+    }
+    POTTS_CK(cudaMemcpyAsync(h->h_rec, h->d_rec, (size_t)(n * rec_len * 8),
+                             cudaMemcpyDeviceToHost, h->stream));
+    POTTS_CK(cudaStreamSynchronize(h->stream));
+    for (int64_t s = 0; s < n; ++s)
+      update_obs(&h->obs, h->h_rec + s * rec_len, h->L, q, true);
+    if (out_counts)
+      std::memcpy(out_counts + done * rec_len, h->h_rec,
+                  (size_t)(n * rec_len * 8));
+    h->sweep += (uint64_t)n;
+    done += n;
+  }
+  h->obs.sweep = h->sweep;
+  return POTTS_OK;
+}
+
+int potts_observables(potts_h h, potts_obs *out) {
+  if (!h || !out) return fail(POTTS_EINVAL, "NULL argument");
+  *out = h->obs;
+  out->sweep = h->sweep;
+  return POTTS_OK;
+}
+
+int potts_reset_averages(potts_h h) {
+  if (!h) return fail(POTTS_EINVAL, "handle is NULL");
+  h->obs.nsamples = 0;
+  h->obs.sum_e = h->obs.sum_e2 = h->obs.sum_e4 = 0;
+  h->obs.sum_m = h->obs.sum_m2 = 0;
+  return POTTS_OK;
+}
+
+int potts_get_spins(potts_h h, uint8_t *out_LxL) {
+  if (!h || !out_LxL) return fail(POTTS_EINVAL, "NULL argument");
+  std::vector<uint8_t> tmp;
+  try {
+    tmp.resize((size_t)(2 * h->plane_bytes));
+  } catch (...) {
+    return fail(POTTS_ENOMEM, "host allocation failed");
+  }
+  POTTS_CK(cudaMemcpyAsync(tmp.data(), h->d_planes, tmp.size(),
+                           cudaMemcpyDeviceToHost, h->stream));
+  POTTS_CK(cudaStreamSynchronize(h->stream));
+  planes_to_rowmajor(tmp.data(), tmp.data() + h->plane_bytes, h->L, out_LxL);
+  return POTTS_OK;
+}
+
+int potts_set_state(potts_h h, const uint8_t *LxL, uint64_t sweep) {
+  if (!h || !LxL) return fail(POTTS_EINVAL, "NULL argument");
+  const int64_t n = (int64_t)h->L * h->L;
+  for (int64_t k = 0; k < n; ++k)
+    if (LxL[k] >= h->q)
+      return fail(POTTS_EINVAL, "spin %d at %lld is >= q = %d", LxL[k],
+                  (long long)k, h->q);
+  std::vector<uint8_t> tmp;
+  try {
+    tmp.resize((size_t)(2 * h->plane_bytes));
+  } catch (...) {
+    return fail(POTTS_ENOMEM, "host allocation failed");
+  }
+  rowmajor_to_planes(LxL, h->L, tmp.data(), tmp.data() + h->plane_bytes);
+  POTTS_CK(cudaMemcpyAsync(h->d_planes, tmp.data(), tmp.size(),
+                           cudaMemcpyHostToDevice, h->stream));
+  POTTS_CK(cudaStreamSynchronize(h->stream));
+  h->sweep = sweep;
+  h->obs.sweep = sweep;
+  return recount_into_obs(h);
+}
+
+int potts_set_stream(potts_h h, void *stream) {
+  if (!h) return fail(POTTS_EINVAL, "handle is NULL");
+  // finish work queued on the old stream before switching
+  POTTS_CK(cudaStreamSynchronize(h->stream));
+  h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+  return POTTS_OK;
+}
+
+int potts_device_planes(potts_h h, void **white, void **black,
+                        int64_t *row_bytes, int32_t *layout) {
+  if (!h) return fail(POTTS_EINVAL, "handle is NULL");
+  if (white) *white = h->d_planes;
+  if (black) *black = h->d_planes + h->plane_bytes;
+  if (row_bytes) *row_bytes = h->H;
+  if (layout) *layout = h->layout;
+  return POTTS_OK;
+}
+
+int potts_destroy(potts_h h) {
+  if (!h) return fail(POTTS_EINVAL, "handle is NULL");
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_lattice(h);
+  return POTTS_OK;
+}
+
+}  // extern "C"
