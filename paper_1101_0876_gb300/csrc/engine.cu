@@ -1,0 +1,589 @@
+// Batched sweep engine (see engine.cuh) and the potts_batch_* entry points.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <new>
+
+#include "engine.cuh"
+
+namespace potts {
+
+// ------------------------------------------------------------- kernel
+// Persistent CTAs walk the flat tile list; every tile belongs to one member
+// and is processed exactly like a tile of the single-lattice pass: the same
+// walk, the same Philox counters, the same reductions into that member's
+// record of sweep s.  Members whose step has fewer than s+1 sweeps skip
+// their tiles.
+// Fewer resident CTAs than the single-lattice pass: the per-tile descriptor
+// and the dispatch over spin classes need more registers.
+#ifndef POTTS_BATCH_MINB
+#define POTTS_BATCH_MINB 4
+#endif
+
+template <int COLOUR>
+__global__ void __launch_bounds__(kPassThreads, POTTS_BATCH_MINB)
+    batch_pass_kernel(const LatDesc *__restrict__ D,
+                      const TileRef *__restrict__ T, int32_t ntiles,
+                      int32_t s) {
+  constexpr bool COUNTS = COLOUR == 1;
+  extern __shared__ uint32_t s_hist[];
+  __shared__ __align__(16) uint32_t s_tab[9 * 4];
+  __shared__ uint32_t s_sat;
+  const uint32_t tid = threadIdx.x;
+  for (int32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const TileRef tr = T[t];
+    const LatDesc &d = D[tr.lat];
+    if (s >= d.nsweeps) continue;  // same for the whole CTA
+    const uint32_t q = (uint32_t)d.q;
+    if (tid < 9) s_tab[tid * 4] = d.tab[tid];
+    for (uint32_t v = tid; v < q * 32u; v += kPassThreads) s_hist[v] = 0;
+    if (tid == 0) s_sat = 0;
+    __syncthreads();
+
+    PassArgs A;
+    A.own = d.plane[COLOUR];
+    A.other = d.plane[COLOUR ^ 1];
+    A.L = d.L;
+    A.H = d.H;
+    A.q = q;
+    A.colour = COLOUR;
+    const uint64_t t0 = ((uint64_t)d.t0_hi << 32 | d.t0_lo) + (uint64_t)s;
+    A.t_lo = (uint32_t)t0;
+    A.t_hi = (uint32_t)(t0 >> 32);
+    A.key0 = d.key0;
+    A.key1 = d.key1;
+    const PhiloxKey ks = philox_schedule(A.key0, A.key1);
+    const int32_t cx = (int32_t)tid % d.CX, rg = (int32_t)tid / d.CX;
+    const int32_t chunk = tr.cx0 + cx;
+    const int32_t i0 = tr.i0 + rg * d.TR;
+    uint32_t ne = 0, rows = 0;
+    if (rg < d.RG && chunk * 16 < d.H && i0 < d.L) {
+      rows = (uint32_t)min(d.TR, d.L - i0);
+      const uint8_t *tab = reinterpret_cast<const uint8_t *>(s_tab);
+      uint32_t *lh = s_hist + (tid & 31u);
+      const int32_t x0 = chunk * 16;
+#define POTTS_WALK(QB, LT)                                                  \
+  walk_column<QB, COLOUR, COUNTS, false, LT>(A, ks, tab, x0, i0, (int)rows, \
+                                              lh, &ne)
+      if (d.lt0) {
+        switch (d.qbits) {
+          case 4: POTTS_WALK(4, true); break;
+          case 5: POTTS_WALK(5, true); break;
+          case 6: POTTS_WALK(6, true); break;
+          case 7: POTTS_WALK(7, true); break;
+          default: POTTS_WALK(8, true); break;
+        }
+      } else {
+        switch (d.qbits) {
+          case 4: POTTS_WALK(4, false); break;
+          case 5: POTTS_WALK(5, false); break;
+          case 6: POTTS_WALK(6, false); break;
+          case 7: POTTS_WALK(7, false); break;
+          default: POTTS_WALK(8, false); break;
+        }
+      }
+#undef POTTS_WALK
+    }
+    unsigned long long *rec = d.rec + (int64_t)s * (1 + d.q);
+    if (COUNTS) {
+      uint32_t sat = 64u * rows - ne;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        sat += __shfl_xor_sync(0xFFFFFFFFu, sat, o);
+      if ((tid & 31u) == 0 && sat) atomicAdd(&s_sat, sat);
+    }
+    __syncthreads();
+    if (COUNTS && tid == 0 && s_sat) atomicAdd(rec, (unsigned long long)s_sat);
+    for (uint32_t v = tid; v < q; v += kPassThreads) {
+      uint32_t sum = 0;
+#pragma unroll 8
+      for (int l = 0; l < 32; ++l) sum += s_hist[v * 32u + l];
+      if (sum) atomicAdd(rec + 1 + v, (unsigned long long)sum);
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_batch_pass(const LatDesc *d_desc, const TileRef *d_tiles,
+                              int32_t ntiles, int32_t colour, int32_t s,
+                              int32_t grid, size_t smem, cudaStream_t st) {
+  if (colour)
+    batch_pass_kernel<1><<<grid, kPassThreads, smem, st>>>(d_desc, d_tiles,
+                                                           ntiles, s);
+  else
+    batch_pass_kernel<0><<<grid, kPassThreads, smem, st>>>(d_desc, d_tiles,
+                                                           ntiles, s);
+  return cudaGetLastError();
+}
+
+int batch_blocks_per_sm(size_t smem) {
+  int a = 0, b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &a, batch_pass_kernel<0>, kPassThreads, smem) != cudaSuccess)
+    a = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &b, batch_pass_kernel<1>, kPassThreads, smem) != cudaSuccess)
+    b = 1;
+  return std::max(1, std::min(a, b));
+}
+
+// ------------------------------------------------------------- engine
+Engine::~Engine() {
+  drop_graph();
+  if (d_desc_) cudaFree(d_desc_);
+  if (h_desc_) cudaFreeHost(h_desc_);
+  if (d_tiles_) cudaFree(d_tiles_);
+  if (d_rec_) cudaFree(d_rec_);
+  if (h_rec_) cudaFreeHost(h_rec_);
+}
+
+void Engine::drop_graph() {
+  if (gexec_) cudaGraphExecDestroy(gexec_);
+  gexec_ = nullptr;
+  graph_k_ = -1;
+}
+
+int Engine::init(cudaStream_t stream) {
+  st_ = stream;
+  sm_count_ = sm_count_of_current_device();
+  return POTTS_OK;
+}
+
+size_t Engine::member_bytes(int32_t L) const {
+  return (size_t)L * (size_t)(L / 2) * 2;
+}
+
+int Engine::create_member(Member *m) {
+  m->plane_bytes = (int64_t)m->L * (m->L / 2);
+  cudaError_t e = cudaMalloc(&m->planes, (size_t)(2 * m->plane_bytes));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    m->planes = nullptr;
+    return fail(POTTS_ENOMEM, "cudaMalloc(%lld bytes) for a member: %s",
+                (long long)(2 * m->plane_bytes), cudaGetErrorString(e));
+  }
+  m->owns_planes = true;
+  if (m->start == POTTS_START_ORDERED) {
+    POTTS_CK(cudaMemsetAsync(m->planes, 0, (size_t)(2 * m->plane_bytes), st_));
+  } else {
+    POTTS_CK(launch_init_random(m->planes, m->plane_bytes, (uint32_t)m->q, 0,
+                                m->seed, st_));
+    POTTS_CK(launch_init_random(m->planes + m->plane_bytes, m->plane_bytes,
+                                (uint32_t)m->q, 1, m->seed, st_));
+  }
+  // initial counts
+  unsigned long long *d = nullptr;
+  POTTS_CK(cudaMallocAsync(&d, (size_t)(1 + m->q) * 8, st_));
+  POTTS_CK(cudaMemsetAsync(d, 0, (size_t)(1 + m->q) * 8, st_));
+  POTTS_CK(launch_recount(m->planes, m->planes + m->plane_bytes, m->L,
+                          m->L / 2, (uint32_t)m->q, d, st_));
+  std::vector<uint64_t> h((size_t)(1 + m->q));
+  POTTS_CK(cudaMemcpyAsync(h.data(), d, h.size() * 8, cudaMemcpyDeviceToHost,
+                           st_));
+  POTTS_CK(cudaFreeAsync(d, st_));
+  POTTS_CK(cudaStreamSynchronize(st_));
+  update_obs(&m->obs, h.data(), m->L, m->q, false);
+  return POTTS_OK;
+}
+
+void Engine::free_member(Member *m) {
+  if (m->planes && m->owns_planes) cudaFree(m->planes);
+  m->planes = nullptr;
+}
+
+void Engine::set_members(const std::vector<Member *> &members) {
+  members_ = members;
+  dirty_ = true;
+}
+
+int Engine::ensure_capacity(int32_t k) {
+  const size_t n = members_.size();
+  if (n > desc_cap_) {
+    if (d_desc_) cudaFree(d_desc_);
+    if (h_desc_) cudaFreeHost(h_desc_);
+    d_desc_ = nullptr;
+    h_desc_ = nullptr;
+    const size_t cap = std::max<size_t>(n, 2 * desc_cap_);
+    POTTS_CK(cudaMalloc(&d_desc_, cap * sizeof(LatDesc)));
+    POTTS_CK(cudaMallocHost(&h_desc_, cap * sizeof(LatDesc)));
+    desc_cap_ = cap;
+    dirty_ = true;
+  }
+  size_t need = 0;
+  int32_t maxq = 2;
+  for (Member *m : members_) {
+    m->rec_off = (int64_t)need;
+    need += (size_t)k * (1 + m->q);
+    maxq = std::max(maxq, m->q);
+  }
+  rec_used_ = need;
+  if (need > rec_cap_) {
+    if (d_rec_) cudaFree(d_rec_);
+    if (h_rec_) cudaFreeHost(h_rec_);
+    d_rec_ = nullptr;
+    h_rec_ = nullptr;
+    const size_t cap = std::max(need, 2 * rec_cap_);
+    POTTS_CK(cudaMalloc(&d_rec_, cap * 8));
+    POTTS_CK(cudaMallocHost(&h_rec_, cap * 8));
+    rec_cap_ = cap;
+    dirty_ = true;
+  }
+  if (maxq != max_q_) dirty_ = true;
+  max_q_ = maxq;
+  return POTTS_OK;
+}
+
+int Engine::rebuild(int32_t k) {
+  // tile list: per member, its row tiles (shape from choose_geom, with the
+  // tuned walk length as a cap)
+  std::vector<TileRef> tiles;
+  for (size_t i = 0; i < members_.size(); ++i) {
+    Member *m = members_[i];
+    const int32_t H = m->L / 2;
+    TileGeom g = choose_geom(m->L, H, m->q, sm_count_, m->TR);
+    LatDesc &d = h_desc_[i];
+    d.CX = g.CX;
+    d.RG = g.RG;
+    d.TR = g.TR;
+    const int32_t nchunks = H / 16;
+    for (int32_t ty = 0; ty < g.ty; ++ty)
+      for (int32_t tx = 0; tx * g.CX < nchunks; ++tx)
+        tiles.push_back(TileRef{(int32_t)i, tx * g.CX, ty * g.RG * g.TR, 0});
+  }
+  // big members first so the tail of the persistent loop is short tiles
+  std::stable_sort(tiles.begin(), tiles.end(),
+                   [&](const TileRef &a, const TileRef &b) {
+                     return members_[a.lat]->L > members_[b.lat]->L;
+                   });
+  ntiles_ = (int32_t)tiles.size();
+  if (tiles.size() > tiles_cap_) {
+    if (d_tiles_) cudaFree(d_tiles_);
+    d_tiles_ = nullptr;
+    POTTS_CK(cudaMalloc(&d_tiles_, tiles.size() * sizeof(TileRef)));
+    tiles_cap_ = tiles.size();
+  }
+  if (!tiles.empty())
+    POTTS_CK(cudaMemcpyAsync(d_tiles_, tiles.data(),
+                             tiles.size() * sizeof(TileRef),
+                             cudaMemcpyHostToDevice, st_));
+  smem_ = (size_t)max_q_ * 32 * sizeof(uint32_t);
+  const int bps = batch_blocks_per_sm(smem_);
+  grid_ = std::max(1, std::min<int32_t>(ntiles_, sm_count_ * bps));
+  drop_graph();
+  dirty_ = false;
+  (void)k;
+  return POTTS_OK;
+}
+
+int Engine::capture(int32_t k) {
+  drop_graph();
+  cudaGraph_t g = nullptr;
+  POTTS_CK(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaMemsetAsync(d_rec_, 0, rec_used_ * 8, st_);
+  for (int32_t s = 0; s < k && e == cudaSuccess; ++s)
+    for (int c = 0; c < 2 && e == cudaSuccess; ++c)
+      e = launch_batch_pass(d_desc_, d_tiles_, ntiles_, c, s, grid_, smem_,
+                            st_);
+  cudaError_t e2 = cudaStreamEndCapture(st_, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(POTTS_ECUDA, "graph capture failed: %s",
+                cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(&gexec_, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    gexec_ = nullptr;
+    return fail(POTTS_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  }
+  graph_k_ = k;
+  return POTTS_OK;
+}
+
+int Engine::step(int32_t k) {
+  if (members_.empty() || k <= 0) return POTTS_OK;
+  int rc = ensure_capacity(k);
+  if (rc) return rc;
+  const bool was_dirty = dirty_;
+  if (dirty_) {
+    rc = rebuild(k);
+    if (rc) return rc;
+  }
+  int32_t kmax = 0;
+  for (size_t i = 0; i < members_.size(); ++i) {
+    Member *m = members_[i];
+    uint64_t thr[5];
+    if (!threshold_table(m->beta, thr))
+      return fail(POTTS_EINVAL, "beta must be finite and >= 0 (got %g)",
+                  m->beta);
+    const AcceptTable T = accept_table(thr);
+    LatDesc &d = h_desc_[i];
+    d.plane[0] = m->planes;
+    d.plane[1] = m->planes + m->plane_bytes;
+    d.L = m->L;
+    d.H = m->L / 2;
+    d.q = m->q;
+    d.qbits = qbits_for(m->q);
+    d.key0 = (uint32_t)m->seed;
+    d.key1 = (uint32_t)(m->seed >> 32);
+    d.t0_lo = (uint32_t)m->sweep;
+    d.t0_hi = (uint32_t)(m->sweep >> 32);
+    d.nsweeps = std::min(m->nsweeps_step, k);
+    d.rec = d_rec_ + m->rec_off;
+    std::memcpy(d.tab, T.tab, sizeof d.tab);
+    d.lt0 = T.rule_lt0;
+    kmax = std::max(kmax, d.nsweeps);
+  }
+  POTTS_CK(cudaMemcpyAsync(d_desc_, h_desc_, members_.size() * sizeof(LatDesc),
+                           cudaMemcpyHostToDevice, st_));
+  if (kmax == k && !was_dirty) {
+    // steady state: replay the captured step
+    if (!gexec_ || graph_k_ != k) {
+      rc = capture(k);
+      if (rc) return rc;
+    }
+    POTTS_CK(cudaGraphLaunch(gexec_, st_));
+  } else {
+    POTTS_CK(cudaMemsetAsync(d_rec_, 0, rec_used_ * 8, st_));
+    for (int32_t s = 0; s < kmax; ++s)
+      for (int c = 0; c < 2; ++c)
+        POTTS_CK(launch_batch_pass(d_desc_, d_tiles_, ntiles_, c, s, grid_,
+                                   smem_, st_));
+  }
+  POTTS_CK(cudaMemcpyAsync(h_rec_, d_rec_, rec_used_ * 8,
+                           cudaMemcpyDeviceToHost, st_));
+  POTTS_CK(cudaStreamSynchronize(st_));
+  for (size_t i = 0; i < members_.size(); ++i) {
+    Member *m = members_[i];
+    const int32_t n = h_desc_[i].nsweeps;
+    for (int32_t s = 0; s < n; ++s)
+      update_obs(&m->obs, h_rec_ + m->rec_off + (int64_t)s * (1 + m->q), m->L,
+                 m->q, true);
+    m->sweep += (uint64_t)n;
+    m->obs.sweep = m->sweep;
+  }
+  return POTTS_OK;
+}
+
+int Engine::copy_spins(const Member *m, uint8_t *out_LxL) {
+  std::vector<uint8_t> tmp;
+  try {
+    tmp.resize((size_t)(2 * m->plane_bytes));
+  } catch (...) {
+    return fail(POTTS_ENOMEM, "host allocation failed");
+  }
+  POTTS_CK(cudaMemcpyAsync(tmp.data(), m->planes, tmp.size(),
+                           cudaMemcpyDeviceToHost, st_));
+  POTTS_CK(cudaStreamSynchronize(st_));
+  planes_to_rowmajor(tmp.data(), tmp.data() + m->plane_bytes, m->L, out_LxL);
+  return POTTS_OK;
+}
+
+// Times candidate (rows per walk, sweeps per graph) pairs on a scratch copy
+// of the members' planes and keeps the fastest.  The members' planes, sweep
+// indices and observables are restored afterwards, so tuning never changes
+// results.
+int Engine::autotune(int32_t max_k) {
+  if (members_.empty()) return POTTS_OK;
+  std::vector<uint8_t *> saved(members_.size(), nullptr);
+  std::vector<uint64_t> sweeps(members_.size());
+  std::vector<potts_obs> obs(members_.size());
+  std::vector<int32_t> nst(members_.size()), trs(members_.size());
+  size_t total = 0;
+  for (Member *m : members_) total += (size_t)(2 * m->plane_bytes);
+  uint8_t *scratch = nullptr;
+  if (cudaMalloc(&scratch, total) != cudaSuccess) {
+    cudaGetLastError();
+    return POTTS_OK;  // no room to tune: keep the defaults
+  }
+  size_t off = 0;
+  for (size_t i = 0; i < members_.size(); ++i) {
+    Member *m = members_[i];
+    saved[i] = scratch + off;
+    off += (size_t)(2 * m->plane_bytes);
+    POTTS_CK(cudaMemcpyAsync(saved[i], m->planes, (size_t)(2 * m->plane_bytes),
+                             cudaMemcpyDeviceToDevice, st_));
+    sweeps[i] = m->sweep;
+    obs[i] = m->obs;
+    nst[i] = m->nsweeps_step;
+    trs[i] = m->TR;
+  }
+  cudaEvent_t e0, e1;
+  POTTS_CK(cudaEventCreate(&e0));
+  POTTS_CK(cudaEventCreate(&e1));
+  const int32_t trc[] = {0, 4, 8, 16, 32};
+  const int32_t kc[] = {1, 4, 16, 64};
+  float best = 1e30f;
+  int32_t best_tr = 0, best_k = std::min<int32_t>(16, max_k);
+  int rc = POTTS_OK;
+  for (int32_t tr : trc) {
+    for (Member *m : members_) m->TR = tr;
+    dirty_ = true;
+    for (int32_t k : kc) {
+      if (k > max_k) continue;
+      for (Member *m : members_) m->nsweeps_step = k;
+      rc = step(k);  // warm-up (and graph capture)
+      if (rc) break;
+      const int reps = std::max(1, 16 / k);
+      POTTS_CK(cudaEventRecord(e0, st_));
+      for (int r = 0; r < reps && rc == POTTS_OK; ++r) rc = step(k);
+      POTTS_CK(cudaEventRecord(e1, st_));
+      POTTS_CK(cudaEventSynchronize(e1));
+      if (rc) break;
+      float ms = 0;
+      POTTS_CK(cudaEventElapsedTime(&ms, e0, e1));
+      const float per = ms / (float)(reps * k);
+      if (per < best) {
+        best = per;
+        best_tr = tr;
+        best_k = k;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (size_t i = 0; i < members_.size(); ++i) {
+    Member *m = members_[i];
+    cudaMemcpyAsync(m->planes, saved[i], (size_t)(2 * m->plane_bytes),
+                    cudaMemcpyDeviceToDevice, st_);
+    m->sweep = sweeps[i];
+    m->obs = obs[i];
+    m->nsweeps_step = nst[i];
+    m->TR = best_tr;
+  }
+  cudaStreamSynchronize(st_);
+  cudaFree(scratch);
+  tuned_tr_ = best_tr;
+  tuned_k_ = best_k;
+  dirty_ = true;
+  (void)trs;
+  return rc;
+}
+
+}  // namespace potts
+
+using namespace potts;
+
+struct potts_batch {
+  Engine eng;
+  std::vector<Member> members;
+  cudaStream_t stream = nullptr;
+  bool tuned = false;
+  ~potts_batch() {
+    for (Member &m : members) eng.free_member(&m);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+static int validate_lattice(int32_t L, int32_t q, int32_t start) {
+  if (L < 32 || L > 65536 || L % 32 != 0)
+    return fail(POTTS_EINVAL, "L must be a multiple of 32 in [32, 65536] (got %d)", L);
+  if (q < 2 || q > 256) return fail(POTTS_EINVAL, "q must be in [2, 256] (got %d)", q);
+  if (start != POTTS_START_ORDERED && start != POTTS_START_RANDOM)
+    return fail(POTTS_EINVAL, "start must be 0 (ordered) or 1 (random)");
+  return POTTS_OK;
+}
+
+extern "C" {
+
+int potts_batch_create(int32_t n, const int32_t *L, const int32_t *q,
+                       const int32_t *start, const uint64_t *seed,
+                       potts_batch_h *out) {
+  if (!out) return fail(POTTS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n <= 0 || !L || !q || !start || !seed)
+    return fail(POTTS_EINVAL, "n must be > 0 and arrays non-NULL");
+  for (int32_t i = 0; i < n; ++i) {
+    int rc = validate_lattice(L[i], q[i], start[i]);
+    if (rc) return fail(rc, "lattice %d: %s", i, potts_last_error());
+  }
+  potts_batch *b = new (std::nothrow) potts_batch();
+  if (!b) return fail(POTTS_ENOMEM, "host allocation failed");
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete b;
+    return fail(POTTS_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+  }
+  b->eng.init(b->stream);
+  b->members.resize((size_t)n);
+  std::vector<Member *> ptrs;
+  for (int32_t i = 0; i < n; ++i) {
+    Member &m = b->members[(size_t)i];
+    m.L = L[i];
+    m.q = q[i];
+    m.start = start[i];
+    m.seed = seed[i];
+    int rc = b->eng.create_member(&m);
+    if (rc) {
+      delete b;
+      return rc;
+    }
+    ptrs.push_back(&m);
+  }
+  b->eng.set_members(ptrs);
+  *out = b;
+  clear_error();
+  return POTTS_OK;
+}
+
+int potts_batch_sweep(potts_batch_h b, const double *beta, int64_t nsweeps,
+                      uint64_t *const *out_counts) {
+  if (!b || !beta) return fail(POTTS_EINVAL, "NULL argument");
+  if (nsweeps < 0) return fail(POTTS_EINVAL, "nsweeps < 0");
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    uint64_t thr[5];
+    if (!threshold_table(beta[i], thr))
+      return fail(POTTS_EINVAL, "beta[%zu] must be finite and >= 0", i);
+    b->members[i].beta = beta[i];
+  }
+  if (nsweeps == 0) return POTTS_OK;
+  if (!b->tuned) {
+    int rc = b->eng.autotune((int32_t)std::min<int64_t>(nsweeps, 64));
+    if (rc) return rc;
+    b->tuned = true;
+  }
+  const int32_t k = std::max<int32_t>(1, b->eng.tuned_k());
+  int64_t done = 0;
+  while (done < nsweeps) {
+    const int32_t n = (int32_t)std::min<int64_t>(k, nsweeps - done);
+    for (Member &m : b->members) m.nsweeps_step = n;
+    int rc = b->eng.step(k);
+    if (rc) return rc;
+    if (out_counts) {
+      for (size_t i = 0; i < b->members.size(); ++i) {
+        if (!out_counts[i]) continue;
+        const Member &m = b->members[i];
+        std::memcpy(out_counts[i] + done * (1 + m.q), b->eng.records(&m),
+                    (size_t)n * (1 + m.q) * 8);
+      }
+    }
+    done += n;
+  }
+  return POTTS_OK;
+}
+
+int potts_batch_get_spins(potts_batch_h b, int32_t i, uint8_t *out_LxL) {
+  if (!b || !out_LxL) return fail(POTTS_EINVAL, "NULL argument");
+  if (i < 0 || (size_t)i >= b->members.size())
+    return fail(POTTS_EINVAL, "lattice index %d out of range", i);
+  return b->eng.copy_spins(&b->members[(size_t)i], out_LxL);
+}
+
+int potts_batch_observables(potts_batch_h b, int32_t i, potts_obs *out) {
+  if (!b || !out) return fail(POTTS_EINVAL, "NULL argument");
+  if (i < 0 || (size_t)i >= b->members.size())
+    return fail(POTTS_EINVAL, "lattice index %d out of range", i);
+  *out = b->members[(size_t)i].obs;
+  out->sweep = b->members[(size_t)i].sweep;
+  return POTTS_OK;
+}
+
+int potts_batch_destroy(potts_batch_h b) {
+  if (!b) return fail(POTTS_EINVAL, "handle is NULL");
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  delete b;
+  return POTTS_OK;
+}
+
+}  // extern "C"

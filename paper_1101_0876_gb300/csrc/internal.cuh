@@ -24,15 +24,26 @@ void clear_error();
   } while (0)
 
 // ---------------------------------------------------------- geometry
-// CTA work shape of a colour pass: CX 16-byte chunks per CTA row, RG row
-// groups per CTA, each thread walking TR rows.  128 threads per CTA.
+// CTA work shape of a colour pass.  A row tile is CX 16-byte chunks wide
+// and RG row groups of TR rows high (128 threads: thread t takes chunk t%CX
+// and row group t/CX, walking TR rows).  gx CTA columns cover the row; gy
+// CTA rows are launched and loop over the ty row tiles (persistent CTAs, so
+// per-CTA set-up such as zeroing the histogram is paid once per CTA).
 struct TileGeom {
   int32_t CX, RG, TR;
-  int32_t gx, gy;  // grid
+  int32_t gx, gy, ty;
+  int32_t pairs;  // histogram bins are (state, state) pairs (q <= 16)
 };
 constexpr int kPassThreads = 128;
 
-TileGeom choose_geom(int32_t L, int32_t H, int32_t sm_count, int32_t tr_hint);
+// Minimum resident CTAs per SM requested from the compiler for the pass
+// kernels (caps registers at 65536 / (128 * POTTS_PASS_MINB) per thread).
+#ifndef POTTS_PASS_MINB
+#define POTTS_PASS_MINB 8
+#endif
+
+TileGeom choose_geom(int32_t L, int32_t H, int32_t q, int32_t sm_count,
+                     int32_t tr_hint);
 
 // Spin-width class: every spin < 2^qbits.
 int qbits_for(int32_t q);
@@ -43,8 +54,9 @@ bool threshold_table(double beta, uint64_t thr[5]);
 AcceptTable accept_table(const uint64_t thr[5]);
 
 // ----------------------------------------------------------- launches
-// One colour pass of one lattice.  rec != nullptr only on the black pass:
-// it receives {B, hist[q]} (added atomically; must start at zero).
+// One colour pass of one lattice.  rec (may be null) receives, added
+// atomically, the histogram of the updated sites and, on the black pass, B;
+// the record {B, hist[q]} of a sweep must start at zero.
 cudaError_t launch_pass(const PassArgs &A, const AcceptTable &T,
                         const TileGeom &G, unsigned long long *rec,
                         cudaStream_t st);

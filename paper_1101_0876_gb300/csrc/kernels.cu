@@ -10,22 +10,30 @@ namespace potts {
 // ------------------------------------------------------------ the pass
 // Grid: (gx, gy) CTAs of 128 threads.  Thread t of CTA (bx, by) owns chunk
 // bx*CX + t%CX (16 bytes) and rows starting at (by*RG + t/CX)*TR.
-// COUNTS (black pass): after the walk, the satisfied-bond count of the
-// updated sites and the per-lane shared histogram are reduced (warp shuffle,
-// shared atomics) and added with one 64-bit atomic per CTA for B and one per
-// non-empty state for the histogram (Sec. 3.4: per-block energies and state
-// counters, summed; here without a second kernel or a CPU-side sum).
-template <int QB, bool COUNTS, bool LT0>
-__global__ void __launch_bounds__(kPassThreads)
+// Each pass histograms the sites it updated (their final values for this
+// sweep); the black pass also reduces the satisfied-bond count of the black
+// sites against the final white spins, which counts every bond once
+// (Sec. 3.4: per-block energies and state counters, here summed with warp
+// shuffles and shared atomics and added with one 64-bit atomic per
+// non-empty bin per CTA, without a second kernel or a CPU-side sum).
+constexpr int kPairBins = 256;
+
+template <int QB, int COLOUR, bool PAIRS, bool LT0>
+__global__ void __launch_bounds__(kPassThreads, POTTS_PASS_MINB)
     pass_kernel(PassArgs A, AcceptTable Tin, TileGeom G,
                 unsigned long long *rec) {
-  extern __shared__ uint32_t s_hist[];  // q * 32 counters (COUNTS only)
-  __shared__ uint32_t s_tab[9];
+  constexpr bool COUNTS = COLOUR == 1;
+  extern __shared__ uint32_t s_hist[];  // bins * 32 (bins = 256 or q)
+  __shared__ __align__(16) uint32_t s_tab[9 * 4];
   __shared__ uint32_t s_sat;
+  __shared__ uint32_t s_fold[16];
   const uint32_t tid = threadIdx.x;
-  if (tid < 9) s_tab[tid] = Tin.tab[tid];
-  if (COUNTS) {
-    for (uint32_t v = tid; v < A.q * 32u; v += kPassThreads) s_hist[v] = 0;
+  const uint32_t bins = PAIRS ? (uint32_t)kPairBins : A.q;
+  const bool hist = rec != nullptr;
+  if (tid < 9) s_tab[tid * 4] = Tin.tab[tid];
+  if (hist) {
+    for (uint32_t v = tid; v < bins * 32u; v += kPassThreads) s_hist[v] = 0;
+    if (tid < 16) s_fold[tid] = 0;
     if (tid == 0) s_sat = 0;
   }
   __syncthreads();
@@ -33,21 +41,42 @@ __global__ void __launch_bounds__(kPassThreads)
   const PhiloxKey ks = philox_schedule(A.key0, A.key1);
   const int32_t cx = (int32_t)tid % G.CX, rg = (int32_t)tid / G.CX;
   const int32_t chunk = (int32_t)blockIdx.x * G.CX + cx;
-  const int32_t i0 = ((int32_t)blockIdx.y * G.RG + rg) * G.TR;
-  uint32_t ne = 0;
-  int32_t rows = 0;
-  if (rg < G.RG && chunk * 16 < A.H && i0 < A.L) {
-    rows = min(G.TR, A.L - i0);
-    walk_column<QB, COUNTS, LT0>(A, ks, s_tab, chunk * 16, i0, rows, s_hist,
-                                 tid & 31u, &ne);
+  uint32_t ne = 0, rows_done = 0;
+  if (rg < G.RG && chunk * 16 < A.H) {
+    for (int32_t tile = blockIdx.y; tile < G.ty; tile += gridDim.y) {
+      const int32_t i0 = (tile * G.RG + rg) * G.TR;
+      if (i0 >= A.L) continue;
+      const int32_t rows = min(G.TR, A.L - i0);
+      walk_column<QB, COLOUR, COUNTS, PAIRS, LT0>(
+          A, ks, reinterpret_cast<const uint8_t *>(s_tab), chunk * 16, i0,
+          rows, hist ? s_hist + (tid & 31u) : nullptr, &ne);
+      rows_done += (uint32_t)rows;
+    }
   }
+  if (!hist) return;
   if (COUNTS) {
-    uint32_t sat = 64u * (uint32_t)rows - ne;
+    uint32_t sat = 64u * rows_done - ne;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sat += __shfl_xor_sync(0xFFFFFFFFu, sat, o);
     if ((tid & 31u) == 0 && sat) atomicAdd(&s_sat, sat);
+  }
+  __syncthreads();
+  if (COUNTS && tid == 0 && s_sat) atomicAdd(rec, (unsigned long long)s_sat);
+  if (PAIRS) {
+    // fold pair bins (v0 | v1 << 4) back to the 16 states
+    for (uint32_t p = tid; p < (uint32_t)kPairBins; p += kPassThreads) {
+      uint32_t sum = 0;
+#pragma unroll 8
+      for (int l = 0; l < 32; ++l) sum += s_hist[p * 32u + l];
+      if (sum) {
+        atomicAdd(&s_fold[p & 15u], sum);
+        atomicAdd(&s_fold[p >> 4], sum);
+      }
+    }
     __syncthreads();
-    if (tid == 0 && s_sat) atomicAdd(rec, (unsigned long long)s_sat);
+    if (tid < A.q && s_fold[tid])
+      atomicAdd(rec + 1 + tid, (unsigned long long)s_fold[tid]);
+  } else {
     for (uint32_t v = tid; v < A.q; v += kPassThreads) {
       uint32_t sum = 0;
 #pragma unroll 8
@@ -57,24 +86,31 @@ __global__ void __launch_bounds__(kPassThreads)
   }
 }
 
+template <int QB, int COLOUR, bool PAIRS>
+static cudaError_t launch_c(const PassArgs &A, const AcceptTable &T,
+                            const TileGeom &G, unsigned long long *rec,
+                            cudaStream_t st) {
+  dim3 grid(G.gx, G.gy), block(kPassThreads);
+  const size_t smem =
+      rec ? (size_t)(PAIRS ? kPairBins : A.q) * 32u * sizeof(uint32_t) : 0;
+  if (T.rule_lt0)
+    pass_kernel<QB, COLOUR, PAIRS, true><<<grid, block, smem, st>>>(A, T, G, rec);
+  else
+    pass_kernel<QB, COLOUR, PAIRS, false><<<grid, block, smem, st>>>(A, T, G, rec);
+  return cudaGetLastError();
+}
+
 template <int QB>
 static cudaError_t launch_qb(const PassArgs &A, const AcceptTable &T,
                              const TileGeom &G, unsigned long long *rec,
                              cudaStream_t st) {
-  dim3 grid(G.gx, G.gy), block(kPassThreads);
-  if (rec) {
-    const size_t smem = (size_t)A.q * 32u * sizeof(uint32_t);
-    if (T.rule_lt0)
-      pass_kernel<QB, true, true><<<grid, block, smem, st>>>(A, T, G, rec);
-    else
-      pass_kernel<QB, true, false><<<grid, block, smem, st>>>(A, T, G, rec);
-  } else {
-    if (T.rule_lt0)
-      pass_kernel<QB, false, true><<<grid, block, 0, st>>>(A, T, G, nullptr);
-    else
-      pass_kernel<QB, false, false><<<grid, block, 0, st>>>(A, T, G, nullptr);
+  if constexpr (QB == 4) {
+    if (G.pairs)
+      return A.colour ? launch_c<QB, 1, true>(A, T, G, rec, st)
+                      : launch_c<QB, 0, true>(A, T, G, rec, st);
   }
-  return cudaGetLastError();
+  return A.colour ? launch_c<QB, 1, false>(A, T, G, rec, st)
+                  : launch_c<QB, 0, false>(A, T, G, rec, st);
 }
 
 cudaError_t launch_pass(const PassArgs &A, const AcceptTable &T,
@@ -97,25 +133,46 @@ int qbits_for(int32_t q) {
   return 8;
 }
 
-TileGeom choose_geom(int32_t L, int32_t H, int32_t sm_count,
+TileGeom choose_geom(int32_t L, int32_t H, int32_t q, int32_t sm_count,
                      int32_t tr_hint) {
   TileGeom g;
   const int32_t nchunks = H / 16;
   g.CX = std::min(nchunks, kPassThreads);
   g.RG = kPassThreads / g.CX;
-  // Aim for a few waves of 16 resident CTAs per SM before lengthening walks.
-  const int64_t walkers = (int64_t)nchunks * L;
-  const int64_t target = (int64_t)std::max(sm_count, 1) * 2048 * 2;
+  g.gx = (nchunks + g.CX - 1) / g.CX;
+  const int64_t max_ctas = (int64_t)std::max(sm_count, 1) * POTTS_PASS_MINB;
+  // Longest walk (<= 32 rows) that still gives every resident CTA about
+  // four row tiles, so that the tiles balance across CTAs.
   int32_t tr = 1;
   if (tr_hint > 0) {
     tr = tr_hint;
   } else {
-    while (tr < 32 && walkers / (2 * tr) >= target) tr *= 2;
+    while (tr < 32) {
+      const int64_t ty = (L + (int64_t)g.RG * 2 * tr - 1) / ((int64_t)g.RG * 2 * tr);
+      if (ty * g.gx < 4 * max_ctas) break;
+      tr *= 2;
+    }
   }
   g.TR = std::min(tr, L);
-  g.gx = (nchunks + g.CX - 1) / g.CX;
-  const int32_t rows_per_cta = g.RG * g.TR;
-  g.gy = (L + rows_per_cta - 1) / rows_per_cta;
+  g.ty = (L + g.RG * g.TR - 1) / (g.RG * g.TR);
+  if ((int64_t)g.ty * g.gx >= 4 * max_ctas) {
+    // plenty of tiles: one tile per CTA, the hardware balances the waves
+    g.gy = g.ty;
+  } else {
+    // few tiles: persistent CTAs, balanced number of tiles each
+    const int64_t gy_max = std::max<int64_t>(1, max_ctas / g.gx);
+    const int64_t rounds = (g.ty + gy_max - 1) / gy_max;
+    g.gy = (int32_t)((g.ty + rounds - 1) / rounds);
+  }
+  if (g.gy > 65535) {
+    g.TR = std::min<int32_t>(L, g.TR * ((g.gy + 65534) / 65535) * 2);
+    g.ty = (L + g.RG * g.TR - 1) / (g.RG * g.TR);
+    g.gy = std::min(g.ty, 65535);
+  }
+  // Pair bins (256 x 32 counters to clear and fold per CTA) pay off only
+  // when a CTA updates many sites.
+  const int64_t sites_per_cta = (int64_t)L * H / ((int64_t)g.gx * g.gy);
+  g.pairs = (q <= 16 && sites_per_cta >= 65536) ? 1 : 0;
   return g;
 }
 
@@ -196,8 +253,8 @@ __global__ void recount_kernel(const uint8_t *white, const uint8_t *black,
       const uint32_t n16 = ne16_sum4<8>(Sw[k] ^ Uw[k], Sw[k] ^ Dw[k],
                                         Sw[k] ^ Cw[k], Sw[k] ^ Wd[k]);
       ne += ((n16 >> 4) * 0x01010101u) >> 24;
-      hist_word(s_hist, tid & 31u, Sw[k]);
-      hist_word(s_hist, tid & 31u, Cw[k]);
+      hist_word<false>(s_hist + (tid & 31u), Sw[k]);
+      hist_word<false>(s_hist + (tid & 31u), Cw[k]);
     }
     sat = 64u - ne;
   }

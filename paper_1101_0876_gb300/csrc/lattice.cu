@@ -214,7 +214,7 @@ int potts_create_ex(int32_t L, int32_t q, int32_t start, uint64_t seed,
     if (e != cudaSuccess) { cudaGetLastError(); h->d_rec = nullptr; rc = fail(POTTS_ENOMEM, "cudaMalloc records: %s", cudaGetErrorString(e)); break; }
     e = cudaMallocHost(&h->h_rec, rec_bytes);
     if (e != cudaSuccess) { cudaGetLastError(); h->h_rec = nullptr; rc = fail(POTTS_ENOMEM, "cudaMallocHost records: %s", cudaGetErrorString(e)); break; }
-    h->geom = choose_geom(L, h->H, sm_count_of_current_device(), 0);
+    h->geom = choose_geom(L, h->H, q, sm_count_of_current_device(), 0);
     if (start == POTTS_START_ORDERED) {
       e = cudaMemsetAsync(h->d_planes, 0, (size_t)(2 * h->plane_bytes), h->stream);
     } else {
@@ -268,8 +268,8 @@ int potts_sweep(potts_h h, double beta, int64_t nsweeps, uint64_t *out_counts) {
       for (int c = 0; c < 2; ++c) {
         A[c].t_lo = (uint32_t)t;
         A[c].t_hi = (uint32_t)(t >> 32);
-        POTTS_CK(launch_pass(A[c], T, h->geom,
-                             c ? h->d_rec + s * rec_len : nullptr, h->stream));
+        POTTS_CK(launch_pass(A[c], T, h->geom, h->d_rec + s * rec_len,
+                             h->stream));
       }
     }
     POTTS_CK(cudaMemcpyAsync(h->h_rec, h->d_rec, (size_t)(n * rec_len * 8),

@@ -42,7 +42,7 @@ struct PassArgs {
   uint32_t key0, key1;   // seed
 };
 
-// Table of the acceptance rule, indexed by dE + 4 (0..8).
+// Acceptance rule, tabulated by dE + 4 (0..8).
 //   rule LE  : accept iff a <= tab[dE+4]   (tab = thr-1 for dE >= 1,
 //                                           0xFFFFFFFF for dE <= 0);
 //              valid whenever every thr[d] >= 1.
@@ -54,9 +54,24 @@ struct AcceptTable {
 };
 
 // ---------------------------------------------------------------- SWAR
+//
+// Per site the decision needs idx = 16 * (4 + dE) (dE = n_old - n_new).
+// With NE_x = [x != neighbour] and EQ_x = [x == neighbour], each neighbour
+// contributes c = NE_new + EQ_old in {0, 1, 2} and the four contributions
+// add up to 4 - n_new + n_old = 4 + dE.  For spins < 2^QB, a = (S ^ N) +
+// (2^QB - 1) holds EQ_old in bit QB inverted and b = (P ^ N) + (2^QB - 1)
+// holds NE_new in bit QB, so c = ((b | ~a) & M) + ((b & ~a) & M) with
+// M = 2^QB per byte (two 3-input logic ops per neighbour, no shifts).
+
+template <int QB>
+struct Swar {
+  static constexpr uint32_t K = 0x01010101u * ((1u << QB) - 1u);
+  static constexpr uint32_t M = 0x01010101u * (1u << QB);
+};
 
 // 16 * [byte != 0] per byte of x = a ^ b, summed over four words (result
-// per byte <= 64).  Every spin byte is < 2^QB.
+// per byte <= 64).  Every spin byte is < 2^QB.  Used for QB >= 6 and for
+// the unequal-neighbour count of the black pass.
 template <int QB>
 __device__ __forceinline__ uint32_t ne16_sum4(uint32_t x0, uint32_t x1,
                                               uint32_t x2, uint32_t x3) {
@@ -77,39 +92,63 @@ __device__ __forceinline__ uint32_t ne16_sum4(uint32_t x0, uint32_t x1,
            (((x2 + K) & M) >> 3) + (((x3 + K) & M) >> 3);
   } else {
     const uint32_t K = 0x7F7F7F7Fu, M = 0x80808080u;
-    auto ne = [&](uint32_t x) {
-      return ((((x & K) + K) | x) & M) >> 3;
-    };
+    auto ne = [&](uint32_t x) { return ((((x & K) + K) | x) & M) >> 3; };
     return ne(x0) + ne(x1) + ne(x2) + ne(x3);
   }
 }
 
-// Updates the four sites of one 32-bit word.  S: own spins; Pw: proposals
-// packed as bytes; U, D, C, W: up, down, centre and side neighbour words;
-// a[b]: acceptance variates.  Returns the new word; *nf16 receives
-// 16 * (number of unequal neighbours after the update) per byte.
-template <int QB, bool WANT_NF, bool LT0>
-__device__ __forceinline__ uint32_t update_word(
-    uint32_t S, uint32_t Pw, const uint32_t a[4], uint32_t U, uint32_t D,
-    uint32_t C, uint32_t W, const uint32_t *tab, uint32_t *nf16) {
-  const uint32_t no = ne16_sum4<QB>(S ^ U, S ^ D, S ^ C, S ^ W);
-  const uint32_t nn = ne16_sum4<QB>(Pw ^ U, Pw ^ D, Pw ^ C, Pw ^ W);
-  // 16 * (4 + dE), dE = n_old - n_new = NE_new - NE_old, in 0..128
-  const uint32_t idx = 0x40404040u + nn - no;
+// idx = 16 * (4 + dE) per byte for the four sites of one word.  With
+// WANT_NO also *no16 = 16 * (number of neighbours unequal to S).
+template <int QB, bool WANT_NO>
+__device__ __forceinline__ uint32_t delta_index(uint32_t S, uint32_t P,
+                                                uint32_t U, uint32_t D,
+                                                uint32_t C, uint32_t W,
+                                                uint32_t *no16) {
+  if constexpr (QB <= 5) {
+    constexpr uint32_t K = Swar<QB>::K, M = Swar<QB>::M;
+    const uint32_t a0 = (S ^ U) + K, a1 = (S ^ D) + K, a2 = (S ^ C) + K,
+                   a3 = (S ^ W) + K;
+    const uint32_t b0 = (P ^ U) + K, b1 = (P ^ D) + K, b2 = (P ^ C) + K,
+                   b3 = (P ^ W) + K;
+    const uint32_t s1 = ((b0 | ~a0) & M) + ((b1 | ~a1) & M) +
+                        ((b2 | ~a2) & M) + ((b3 | ~a3) & M);
+    const uint32_t s2 = ((b0 & ~a0) & M) + ((b1 & ~a1) & M) +
+                        ((b2 & ~a2) & M) + ((b3 & ~a3) & M);
+    if (WANT_NO) {
+      const uint32_t n = (a0 & M) + (a1 & M) + (a2 & M) + (a3 & M);
+      *no16 = QB == 4 ? n : n >> 1;
+    }
+    return QB == 4 ? s1 + s2 : (s1 >> 1) + (s2 >> 1);
+  } else {
+    const uint32_t no = ne16_sum4<QB>(S ^ U, S ^ D, S ^ C, S ^ W);
+    const uint32_t nn = ne16_sum4<QB>(P ^ U, P ^ D, P ^ C, P ^ W);
+    if (WANT_NO) *no16 = no;
+    return 0x40404040u + nn - no;
+  }
+}
+
+// Acceptance of the four sites of one word: byte b of the result is 0xFF
+// if site b accepts its proposal.  tab: shared table, entry for dE + 4 = k
+// at byte offset 16 k (so the idx byte is the offset itself).
+template <bool LT0>
+__device__ __forceinline__ uint32_t accept_mask(uint32_t idx, uint32_t a0,
+                                                uint32_t a1, uint32_t a2,
+                                                uint32_t a3,
+                                                const uint8_t *tab) {
+  const uint32_t a[4] = {a0, a1, a2, a3};
   uint32_t m = 0;
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
-    const uint32_t ib = (idx >> (8 * b)) & 0xFFu;
-    const uint32_t t = tab[ib >> 4];
+    const uint32_t off = __byte_perm(idx, 0u, 0x4440u + (uint32_t)b);
+    const uint32_t t = *reinterpret_cast<const uint32_t *>(tab + off);
     bool acc;
     if (LT0)
-      acc = (ib <= 64u) || (a[b] < t);
+      acc = (a[b] < t) || (off <= 64u);
     else
       acc = a[b] <= t;
-    m |= acc ? (0xFFu << (8 * b)) : 0u;
+    if (acc) m |= 0xFFu << (8 * b);
   }
-  if (WANT_NF) *nf16 = no ^ ((no ^ nn) & m);
-  return S ^ ((S ^ Pw) & m);
+  return m;
 }
 
 __device__ __forceinline__ uint32_t pack4(uint32_t p0, uint32_t p1,
@@ -119,12 +158,22 @@ __device__ __forceinline__ uint32_t pack4(uint32_t p0, uint32_t p1,
   return __byte_perm(lo, hi, 0x5410u);
 }
 
-// Counts state v of every byte of w into the per-lane shared histogram.
-__device__ __forceinline__ void hist_word(uint32_t *s_hist, uint32_t lane,
-                                          uint32_t w) {
+// Histogram of the four spins of w into per-lane shared counters.
+// PAIRS (q <= 16): the two nibble-sized spins of sites (0,1) and (2,3) form
+// one 8-bit bin each, so a word costs two shared atomics; the pair bins are
+// folded back to states at the end of the CTA.
+template <bool PAIRS>
+__device__ __forceinline__ void hist_word(uint32_t *lane_hist, uint32_t w) {
+  if (PAIRS) {
+    const uint32_t t = w + __umulhi(w, 1u << 28);  // byte0 = v0 | v1 << 4
+    atomicAdd(lane_hist + (t & 0xFFu) * 32u, 1u);
+    atomicAdd(lane_hist + __byte_perm(t, 0u, 0x4442u) * 32u, 1u);
+  } else {
 #pragma unroll
-  for (int b = 0; b < 4; ++b)
-    atomicAdd(&s_hist[((w >> (8 * b)) & 0xFFu) * 32u + lane], 1u);
+    for (int b = 0; b < 4; ++b)
+      atomicAdd(lane_hist + __byte_perm(w, 0u, 0x4440u + (uint32_t)b) * 32u,
+                1u);
+  }
 }
 
 __device__ __forceinline__ uint4 ld_stream(const uint8_t *p) {
@@ -137,87 +186,140 @@ __device__ __forceinline__ void st_stream(uint8_t *p, uint4 v) {
   __stcs(reinterpret_cast<uint4 *>(p), v);
 }
 
-// Walks rows [i0, i0 + rows) of the 16-byte column starting at byte x0.
-// COUNTS: accumulate the unequal-neighbour total of the updated sites into
-// *ne_total and the final states of the updated sites and of the
-// other-plane sites at the same (i, x) into s_hist.
-template <int QB, bool COUNTS, bool LT0>
+// Per-thread walk state: the three other-plane rows around the current row
+// and the current own row, plus pointers to the next rows.
+struct Walk {
+  uint4 Up, Ce, S;
+  const uint8_t *oth_next;  // other plane, row i+1
+  const uint8_t *oth_cur;   // other plane, row i
+  uint8_t *own_cur;         // own plane, row i
+  int32_t i;                // current row
+};
+
+// One row: update the 16 sites of the own row i against Up (i-1), Ce (i),
+// the freshly loaded row i+1 and the side byte.  LEFT: the side neighbour
+// is at x-1 (row parity + colour even), else at x+1.
+template <int QB, bool LEFT, bool COUNTS, bool PAIRS, bool LT0>
+__device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
+                                       const uint8_t *tab, Walk &w,
+                                       int32_t x0, int32_t xl, int32_t xr,
+                                       bool more, uint32_t *lane_hist,
+                                       uint32_t &ne_acc) {
+  const int32_t L = A.L, H = A.H;
+  const uint4 Dn = ld_other(w.oth_next);
+  const uint32_t ew = __ldg(reinterpret_cast<const uint32_t *>(
+      w.oth_cur - x0 + (LEFT ? xl : xr)));
+  uint8_t *own_next = (w.i + 1 == L) ? A.own + x0 : w.own_cur + H;
+  uint4 Sn = w.S;
+  if (more) Sn = ld_stream(own_next);
+
+  const uint32_t Cw[4] = {w.Ce.x, w.Ce.y, w.Ce.z, w.Ce.w};
+  uint32_t Wd[4];
+  if (LEFT) {
+    Wd[0] = __funnelshift_l(ew, Cw[0], 8);
+    Wd[1] = __funnelshift_l(Cw[0], Cw[1], 8);
+    Wd[2] = __funnelshift_l(Cw[1], Cw[2], 8);
+    Wd[3] = __funnelshift_l(Cw[2], Cw[3], 8);
+  } else {
+    Wd[0] = __funnelshift_r(Cw[0], Cw[1], 8);
+    Wd[1] = __funnelshift_r(Cw[1], Cw[2], 8);
+    Wd[2] = __funnelshift_r(Cw[2], Cw[3], 8);
+    Wd[3] = __funnelshift_r(Cw[3], ew, 8);
+  }
+  const uint32_t Uw[4] = {w.Up.x, w.Up.y, w.Up.z, w.Up.w};
+  const uint32_t Dw[4] = {Dn.x, Dn.y, Dn.z, Dn.w};
+  const uint32_t Sw[4] = {w.S.x, w.S.y, w.S.z, w.S.w};
+  const uint32_t g0 = (uint32_t)(((int64_t)w.i * H + x0) >> 2);
+  uint32_t Nw[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint4 u = philox10(g0 + (uint32_t)k, A.t_lo, A.colour, A.t_hi, ks);
+    const uint64_t r0 = (uint64_t)u.x * A.q, r1 = (uint64_t)u.y * A.q;
+    const uint64_t r2 = (uint64_t)u.z * A.q, r3 = (uint64_t)u.w * A.q;
+    const uint32_t P = pack4((uint32_t)(r0 >> 32), (uint32_t)(r1 >> 32),
+                             (uint32_t)(r2 >> 32), (uint32_t)(r3 >> 32));
+    uint32_t no16 = 0;
+    const uint32_t idx = delta_index<QB, COUNTS>(Sw[k], P, Uw[k], Dw[k],
+                                                 Cw[k], Wd[k], &no16);
+    const uint32_t m = accept_mask<LT0>(idx, (uint32_t)r0, (uint32_t)r1,
+                                        (uint32_t)r2, (uint32_t)r3, tab);
+    Nw[k] = (P & m) | (Sw[k] & ~m);
+    if (COUNTS) {
+      // unequal neighbours after the update: NE_new where accepted
+      const uint32_t nn16 = idx + no16 - 0x40404040u;
+      const uint32_t nf16 = (nn16 & m) | (no16 & ~m);
+      ne_acc += __umulhi(nf16, 1u << 28);  // += nf16 >> 4 (<= 4 per byte)
+    }
+  }
+  st_stream(w.own_cur, make_uint4(Nw[0], Nw[1], Nw[2], Nw[3]));
+  if (lane_hist) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) hist_word<PAIRS>(lane_hist, Nw[k]);
+  }
+  // advance
+  w.Up = w.Ce;
+  w.Ce = Dn;
+  w.S = Sn;
+  w.oth_cur = w.oth_next;
+  w.oth_next = (w.i + 2 >= L) ? A.other + x0 + (int64_t)(w.i + 2 - L) * H
+                              : w.oth_next + H;
+  w.own_cur = own_next;
+  w.i += 1;
+}
+
+// Walks rows [i0, i0 + rows) of the 16-byte column starting at byte x0 of
+// the plane of colour COLOUR.  lane_hist (may be null): per-lane histogram
+// counters of the updated sites.  COUNTS (black pass): *ne_total receives
+// the number of unequal (site, neighbour) pairs after the update.
+template <int QB, int COLOUR, bool COUNTS, bool PAIRS, bool LT0>
 __device__ __forceinline__ void walk_column(const PassArgs &A,
                                             const PhiloxKey &ks,
-                                            const uint32_t *tab, int32_t x0,
+                                            const uint8_t *tab, int32_t x0,
                                             int32_t i0, int32_t rows,
-                                            uint32_t *s_hist, uint32_t lane,
+                                            uint32_t *lane_hist,
                                             uint32_t *ne_total) {
   const int32_t L = A.L, H = A.H;
-  const uint8_t *other = A.other;
-  uint8_t *own = A.own;
   const int32_t xl = (x0 == 0) ? H - 4 : x0 - 4;    // word holding x0-1
   const int32_t xr = (x0 + 16 == H) ? 0 : x0 + 16;  // word holding x0+16
-
-  int32_t im = (i0 == 0) ? L - 1 : i0 - 1;
-  uint4 Up = ld_other(other + (int64_t)im * H + x0);
-  uint4 Ce = ld_other(other + (int64_t)i0 * H + x0);
-  uint4 S = ld_stream(own + (int64_t)i0 * H + x0);
-
-  for (int32_t r = 0; r < rows; ++r) {
-    const int32_t i = i0 + r;
-    const int32_t ip = (i + 1 == L) ? 0 : i + 1;
-    const uint4 Dn = ld_other(other + (int64_t)ip * H + x0);
-    const bool left = ((i + (int32_t)A.colour) & 1) == 0;
-    const uint32_t ew = __ldg(reinterpret_cast<const uint32_t *>(
-        other + (int64_t)i * H + (left ? xl : xr)));
-    uint4 Sn = S;
-    if (r + 1 < rows) Sn = ld_stream(own + (int64_t)ip * H + x0);
-
-    // side-neighbour words
-    uint32_t Wd[4];
-    const uint32_t Cw[4] = {Ce.x, Ce.y, Ce.z, Ce.w};
-    if (left) {
-      Wd[0] = __funnelshift_l(ew, Cw[0], 8);
-      Wd[1] = __funnelshift_l(Cw[0], Cw[1], 8);
-      Wd[2] = __funnelshift_l(Cw[1], Cw[2], 8);
-      Wd[3] = __funnelshift_l(Cw[2], Cw[3], 8);
-    } else {
-      Wd[0] = __funnelshift_r(Cw[0], Cw[1], 8);
-      Wd[1] = __funnelshift_r(Cw[1], Cw[2], 8);
-      Wd[2] = __funnelshift_r(Cw[2], Cw[3], 8);
-      Wd[3] = __funnelshift_r(Cw[3], ew, 8);
-    }
-    const uint32_t Uw[4] = {Up.x, Up.y, Up.z, Up.w};
-    const uint32_t Dw[4] = {Dn.x, Dn.y, Dn.z, Dn.w};
-    const uint32_t Sw[4] = {S.x, S.y, S.z, S.w};
-    uint32_t Nw[4];
-    const uint32_t g0 = (uint32_t)(((int64_t)i * H + x0) >> 2);
-    uint32_t ne_acc = 0;
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      const uint4 u = philox10(g0 + (uint32_t)w, A.t_lo, A.colour, A.t_hi, ks);
-      const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
-      uint32_t p[4], a[4];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const uint64_t prod = (uint64_t)uw[b] * A.q;
-        p[b] = (uint32_t)(prod >> 32);
-        a[b] = (uint32_t)prod;
+  Walk w;
+  const int32_t im = (i0 == 0) ? L - 1 : i0 - 1;
+  const int32_t ip = (i0 + 1 == L) ? 0 : i0 + 1;
+  w.oth_cur = A.other + (int64_t)i0 * H + x0;
+  w.oth_next = A.other + (int64_t)ip * H + x0;
+  w.own_cur = A.own + (int64_t)i0 * H + x0;
+  w.Up = ld_other(A.other + (int64_t)im * H + x0);
+  w.Ce = ld_other(w.oth_cur);
+  w.S = ld_stream(w.own_cur);
+  w.i = i0;
+  uint32_t ne_acc = 0;
+  int32_t r = 0;
+  // Side neighbour at x-1 when (i + colour) is even.  Walks start on even
+  // rows when rows is even, so pairs of rows have a fixed pattern.
+  if ((i0 & 1) == 0) {
+    for (; r + 2 <= rows; r += 2) {
+      do_row<QB, COLOUR == 0, COUNTS, PAIRS, LT0>(A, ks, tab, w, x0, xl, xr,
+                                                  true, lane_hist, ne_acc);
+      do_row<QB, COLOUR == 1, COUNTS, PAIRS, LT0>(A, ks, tab, w, x0, xl, xr,
+                                                  r + 2 < rows, lane_hist,
+                                                  ne_acc);
+      if (COUNTS) {
+        *ne_total += (ne_acc * 0x01010101u) >> 24;
+        ne_acc = 0;
       }
-      const uint32_t Pw = pack4(p[0], p[1], p[2], p[3]);
-      uint32_t nf16 = 0;
-      Nw[w] = update_word<QB, COUNTS, LT0>(Sw[w], Pw, a, Uw[w], Dw[w], Cw[w],
-                                           Wd[w], tab, &nf16);
-      if (COUNTS) ne_acc += nf16 >> 4;
     }
-    st_stream(own + (int64_t)i * H + x0, make_uint4(Nw[0], Nw[1], Nw[2], Nw[3]));
+  }
+  for (; r < rows; ++r) {
+    const bool left = ((w.i + COLOUR) & 1) == 0;
+    if (left)
+      do_row<QB, true, COUNTS, PAIRS, LT0>(A, ks, tab, w, x0, xl, xr,
+                                           r + 1 < rows, lane_hist, ne_acc);
+    else
+      do_row<QB, false, COUNTS, PAIRS, LT0>(A, ks, tab, w, x0, xl, xr,
+                                            r + 1 < rows, lane_hist, ne_acc);
     if (COUNTS) {
       *ne_total += (ne_acc * 0x01010101u) >> 24;
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        hist_word(s_hist, lane, Nw[w]);
-        hist_word(s_hist, lane, Cw[w]);
-      }
+      ne_acc = 0;
     }
-    Up = Ce;
-    Ce = Dn;
-    S = Sn;
   }
 }
 

@@ -328,17 +328,24 @@ class Server:
             raise
 
     def poll(self, rid: int, max_sweeps: int = 4096):
-        """Returns (records array (n, 1+q), done)."""
-        q = self._q[rid]
-        out = np.empty((int(max_sweeps), 1 + q), dtype=np.uint64)
+        """Returns (records array (n, 1+q), done).  Raises PottsError for a
+        cancelled, failed or unknown request."""
+        q = self._q.get(rid)
         n = ctypes.c_int64()
         done = ctypes.c_int()
-        check(lib().potts_serve_poll(self._h, int(rid),
-                                     _ptr(out, ctypes.c_uint64),
-                                     int(max_sweeps), ctypes.byref(n),
-                                     ctypes.byref(done)))
+        if q is None:
+            check(lib().potts_serve_poll(self._h, int(rid),
+                                         ctypes.POINTER(ctypes.c_uint64)(), 0,
+                                         ctypes.byref(n), ctypes.byref(done)))
+            return np.empty((0, 0), dtype=np.uint64), bool(done.value)
+        out = np.empty((int(max_sweeps), 1 + q), dtype=np.uint64)
+        rc = lib().potts_serve_poll(self._h, int(rid),
+                                    _ptr(out, ctypes.c_uint64),
+                                    int(max_sweeps), ctypes.byref(n),
+                                    ctypes.byref(done))
         if done.value:
             self._q.pop(rid, None)
+        check(rc)
         return out[:n.value], bool(done.value)
 
     def cancel(self, rid: int) -> None:
