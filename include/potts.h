@@ -144,6 +144,32 @@ int potts_device_planes(potts_h h, void **white, void **black,
 
 int potts_destroy(potts_h h);
 
+/* Sweeps a lattice held in caller-owned device memory without allocating
+ * anything (the paper has no counterpart: it exists for callers that cannot
+ * allocate device memory when they sweep, e.g. code running during CUDA
+ * graph capture, or inside a framework whose caching allocator already
+ * holds the device memory).
+ * white, black: device pointers (16-byte aligned) to the two colour planes
+ *   in the POTTS_LAYOUT_U8 layout (L rows x L/2 bytes each, row i of the
+ *   white plane holding the sites (i, j) with i + j even in order of j);
+ *   read and updated in place.
+ * sweep: global index of the first sweep; seed, beta as for potts_sweep.
+ * out_counts: NULL, or host or device memory for nsweeps * (1 + q) uint64
+ *   records {B, hist[0..q-1]}.
+ * stream: a cudaStream_t or NULL (legacy default stream); the call returns
+ *   after the work on it has finished.
+ * Limit: nsweeps * (1 + q) <= 8192 per call (the records accumulate in a
+ *   fixed 64 KiB device array that every device loading the library holds
+ *   until exit); larger requests fail with POTTS_EINVAL.  All calls on a
+ *   device share that array, so calls that overlap on the GPU (different
+ *   streams or threads) race; serialise them.  The first call on a device
+ *   looks up the array's device address; make that first call before any
+ *   stream capture.  Results equal potts_sweep's bit for bit. */
+int potts_sweep_planes_noalloc(void *white, void *black, int32_t L, int32_t q,
+                               uint64_t seed, uint64_t sweep, double beta,
+                               int64_t nsweeps, uint64_t *out_counts,
+                               void *stream);
+
 /* ------------------------------------------------------------------ batch
  * n independent lattices (the paper's "several samples", Sec. 3) swept
  * together: every colour pass of every lattice runs in one persistent

@@ -89,6 +89,10 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_void_p),
                                            _i64p, _i32p]),
     "potts_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "potts_sweep_planes_noalloc": (ctypes.c_int, [
+        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+        ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int64,
+        _u64p, ctypes.c_void_p]),
     "potts_batch_create": (ctypes.c_int, [ctypes.c_int32, _i32p, _i32p,
                                           _i32p, _u64p,
                                           ctypes.POINTER(ctypes.c_void_p)]),
@@ -158,6 +162,23 @@ def _ptr(a: np.ndarray, ct):
 def threshold_table(beta: float) -> np.ndarray:
     out = np.zeros(5, dtype=np.uint64)
     check(lib().potts_threshold_table(float(beta), _ptr(out, ctypes.c_uint64)))
+    return out
+
+
+def sweep_planes_noalloc(white_ptr: int, black_ptr: int, L: int, q: int,
+                         seed: int, sweep: int, beta: float, nsweeps: int,
+                         out: np.ndarray | None = None,
+                         stream: int | None = None):
+    """Sweeps caller-owned device planes without any allocation in the
+    library (potts_sweep_planes_noalloc).  Returns the (nsweeps, 1+q)
+    records, in `out` if given."""
+    if out is None:
+        out = np.empty((int(nsweeps), 1 + int(q)), dtype=np.uint64)
+    assert out.dtype == np.uint64 and out.flags.c_contiguous
+    check(lib().potts_sweep_planes_noalloc(
+        ctypes.c_void_p(white_ptr), ctypes.c_void_p(black_ptr), int(L),
+        int(q), int(seed), int(sweep), float(beta), int(nsweeps),
+        _ptr(out, ctypes.c_uint64), ctypes.c_void_p(stream or None)))
     return out
 
 
