@@ -169,14 +169,21 @@ def init_dist(ws, backend):
     return dist
 
 
-def reduce_max(x: float, ws: int, device) -> float:
+def reduce_max(x: float, ws: int, device=None) -> float:
+    """Max over ranks (the slowest rank sets the job's time)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device=device)
+    t = torch.tensor([x], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_seed(base: int, rank: int) -> int:
+    """Each rank sweeps its own independent replica (weak scaling)."""
+    return base + rank
 
 
 def barrier(ws):
@@ -211,7 +218,7 @@ def run_ours(args):
     cfg = workloads.PAPER_Q9
     L, q = args.L or cfg.L, cfg.q
     N = L * L
-    seed = cfg.seed + rank          # each rank its own replica
+    seed = replica_seed(cfg.seed, rank)
     temps = cfg.t_over_tc
     betas = [workloads.beta_at(q, t) for t in temps]
 
@@ -324,6 +331,12 @@ def run_ours(args):
                      "bytes_per_launch": bytes_per_launch},
         "clocks": clocks.summary(),
     }
+    if ws == 1 and not args.no_batched:
+        lat.close()
+        line["batched"] = measure_batched(args, line["updates_per_s"])
+    if ws == 1 and not args.no_served:
+        lat.close()
+        line["served"] = measure_served(args, line["updates_per_s"])
     if not args.no_cpu_baseline and ws == 1:
         Lc, sweeps = args.cpu_L, args.cpu_sweeps
         nsu, dt = cpu_oracle_ns_per_update(Lc, q, betas[1], sweeps, cfg.seed)
@@ -333,6 +346,75 @@ def run_ours(args):
                       f"{sweeps} sweeps ({dt:.1f} s); per-update cost of the "
                       f"serial raster loop does not depend on L"}
     return line
+
+
+# ------------------------------------------------- batched / served
+def measure_batched(args, single_updates_per_s):
+    """The batched configuration: 256 lattices (L log-uniform in [64, 2048],
+    q in {6, 9, 15, 24}, T in [0.98, 1.02] T_c, seeds 1000 + i) swept
+    together; the first call (which autotunes) is a warm-up, the second
+    (500 sweeps) is timed end to end through potts_batch_sweep."""
+    from paper_1101_0876_gb300 import potts, workloads
+    spec = workloads.batched(sweeps=args.batch_sweeps)
+    b = potts.Batch(spec.L, spec.q, spec.start, spec.seed)
+    b.sweep(spec.beta, 20, records=False)
+    t0 = time.perf_counter()
+    b.sweep(spec.beta, spec.sweeps)
+    dt = time.perf_counter() - t0
+    upd = sum(L * L for L in spec.L) * spec.sweeps
+    b.close()
+    return {"lattices": len(spec.L), "sweeps": spec.sweeps,
+            "updates": upd, "seconds": dt, "updates_per_s": upd / dt,
+            "ratio_to_single": (upd / dt) / single_updates_per_s,
+            "timing": "wall clock around potts_batch_sweep, records to host"}
+
+
+def measure_served(args, single_updates_per_s):
+    """The served configuration, bounded: the first `served_requests`
+    requests of the Poisson stream (200 req/s; L log-uniform in
+    [128, 8192]; q in {6, 9, 15, 24, 96}; T in [0.97, 1.03] T_c; nsweeps in
+    [100, 5000]; seed = request id), submitted at their arrival times to a
+    continuous-batching server with a 120 GB budget; latency = time the
+    last record was polled - arrival time."""
+    from paper_1101_0876_gb300 import potts, workloads
+    reqs = workloads.served(n=args.served_requests)
+    srv = potts.Server(hbm_budget_bytes=120 * 10**9,
+                       max_slots=args.served_slots,
+                       sweeps_per_step=args.served_k)
+    t0 = time.perf_counter()
+    nxt = 0
+    live = {}
+    lat = []
+    while nxt < len(reqs) or live:
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt].arrival_s <= now:
+            r = reqs[nxt]
+            rid = srv.submit(r.L, r.q, r.beta, r.nsweeps, r.seed, r.start)
+            live[rid] = r
+            nxt += 1
+        for rid in list(live):
+            _, done = srv.poll(rid, max_sweeps=8192)
+            if done:
+                lat.append(time.perf_counter() - t0 - live.pop(rid).arrival_s)
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.stop()
+    upd = sum(r.L * r.L * r.nsweeps for r in reqs)
+    lat_ms = sorted(1e3 * x for x in lat)
+
+    def pct(p):
+        return lat_ms[min(len(lat_ms) - 1, int(round(p / 100 * (len(lat_ms) - 1))))]
+    busy = wall - reqs[0].arrival_s
+    return {"requests": len(reqs), "updates": upd,
+            "seconds": busy, "updates_per_s": upd / busy,
+            "ratio_to_single": (upd / busy) / single_updates_per_s,
+            "p50_ms": pct(50), "p99_ms": pct(99), "max_ms": lat_ms[-1],
+            "offered_updates_per_s": upd / max(reqs[-1].arrival_s, 1e-9),
+            "slots": args.served_slots, "sweeps_per_step": args.served_k,
+            "steps": st["steps"],
+            "note": "offered load exceeds capacity: latency grows with the "
+                    "backlog (saturated server)"}
 
 
 # --------------------------------------------------- reference arm
@@ -405,6 +487,12 @@ def main():
     ap.add_argument("--cpu-L", type=int, default=2048)
     ap.add_argument("--cpu-sweeps", type=int, default=40)
     ap.add_argument("--ref-L", type=int, default=1024)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--batch-sweeps", type=int, default=500)
+    ap.add_argument("--served-requests", type=int, default=200)
+    ap.add_argument("--served-slots", type=int, default=32)
+    ap.add_argument("--served-k", type=int, default=32)
     ap.add_argument("--rng-ceiling", action="store_true",
                     help="time the random-number work alone and exit")
     args = ap.parse_args()

@@ -9,132 +9,122 @@
 namespace potts {
 
 // ------------------------------------------------------------- kernel
-// Persistent CTAs walk the flat tile list; every tile belongs to one member
-// and is processed exactly like a tile of the single-lattice pass: the same
-// walk, the same Philox counters, the same reductions into that member's
-// record of sweep s.  Members whose step has fewer than s+1 sweeps skip
-// their tiles.
-// Fewer resident CTAs than the single-lattice pass: the per-tile descriptor
-// and the dispatch over spin classes need more registers.
+// One CTA per row tile.  The CTA finds its member by a binary search over
+// the tile offsets in the parameter block (uniform), then runs exactly the
+// walk, Philox counters and reductions of the single-lattice pass on that
+// tile, into the member's record of sweep s.  Members whose step has fewer
+// than s+1 sweeps return at once.
 #ifndef POTTS_BATCH_MINB
 #define POTTS_BATCH_MINB 4
 #endif
 
-template <int COLOUR>
+template <int COLOUR, bool LT0>
 __global__ void __launch_bounds__(kPassThreads, POTTS_BATCH_MINB)
-    batch_pass_kernel(const LatDesc *__restrict__ D,
-                      const TileRef *__restrict__ T, int32_t ntiles,
-                      int32_t s) {
+    batch_pass_kernel(const __grid_constant__ LaunchParams P,
+                      const StepDesc *__restrict__ S, int32_t s) {
   constexpr bool COUNTS = COLOUR == 1;
   extern __shared__ uint32_t s_hist[];
   __shared__ __align__(16) uint32_t s_tab[9 * 4];
   __shared__ uint32_t s_sat;
   const uint32_t tid = threadIdx.x;
-  for (int32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const TileRef tr = T[t];
-    const LatDesc &d = D[tr.lat];
-    if (s >= d.nsweeps) continue;  // same for the whole CTA
-    const uint32_t q = (uint32_t)d.q;
-    if (tid < 9) s_tab[tid * 4] = d.tab[tid];
-    for (uint32_t v = tid; v < q * 32u; v += kPassThreads) s_hist[v] = 0;
-    if (tid == 0) s_sat = 0;
-    __syncthreads();
+  const int32_t bid = (int32_t)blockIdx.x;
+  int32_t lo = 0, hi = P.n - 1;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (P.m[mid].tile0 <= bid) lo = mid;
+    else hi = mid - 1;
+  }
+  const StaticDesc &d = P.m[lo];
+  const StepDesc &sd = S[d.step];
+  if (s >= sd.nsweeps) return;  // same for the whole CTA
+  const uint32_t q = (uint32_t)d.q;
+  if (tid < 9) s_tab[tid * 4] = sd.tab[tid];
+  for (uint32_t v = tid; v < q * 32u; v += kPassThreads) s_hist[v] = 0;
+  if (tid == 0) s_sat = 0;
+  __syncthreads();
 
-    PassArgs A;
-    A.own = d.plane[COLOUR];
-    A.other = d.plane[COLOUR ^ 1];
-    A.L = d.L;
-    A.H = d.H;
-    A.q = q;
-    A.colour = COLOUR;
-    const uint64_t t0 = ((uint64_t)d.t0_hi << 32 | d.t0_lo) + (uint64_t)s;
-    A.t_lo = (uint32_t)t0;
-    A.t_hi = (uint32_t)(t0 >> 32);
-    A.key0 = d.key0;
-    A.key1 = d.key1;
-    const PhiloxKey ks = philox_schedule(A.key0, A.key1);
-    const int32_t cx = (int32_t)tid % d.CX, rg = (int32_t)tid / d.CX;
-    const int32_t chunk = tr.cx0 + cx;
-    const int32_t i0 = tr.i0 + rg * d.TR;
-    uint32_t ne = 0, rows = 0;
-    if (rg < d.RG && chunk * 16 < d.H && i0 < d.L) {
-      rows = (uint32_t)min(d.TR, d.L - i0);
-      const uint8_t *tab = reinterpret_cast<const uint8_t *>(s_tab);
-      uint32_t *lh = s_hist + (tid & 31u);
-      const int32_t x0 = chunk * 16;
-#define POTTS_WALK(QB, LT)                                                  \
-  walk_column<QB, COLOUR, COUNTS, false, LT>(A, ks, tab, x0, i0, (int)rows, \
-                                              lh, &ne)
-      if (d.lt0) {
-        switch (d.qbits) {
-          case 4: POTTS_WALK(4, true); break;
-          case 5: POTTS_WALK(5, true); break;
-          case 6: POTTS_WALK(6, true); break;
-          case 7: POTTS_WALK(7, true); break;
-          default: POTTS_WALK(8, true); break;
-        }
-      } else {
-        switch (d.qbits) {
-          case 4: POTTS_WALK(4, false); break;
-          case 5: POTTS_WALK(5, false); break;
-          case 6: POTTS_WALK(6, false); break;
-          case 7: POTTS_WALK(7, false); break;
-          default: POTTS_WALK(8, false); break;
-        }
-      }
-#undef POTTS_WALK
+  PassArgs A;
+  A.own = d.plane[COLOUR];
+  A.other = d.plane[COLOUR ^ 1];
+  A.L = d.L;
+  A.H = d.H;
+  A.q = q;
+  A.colour = COLOUR;
+  const uint64_t t0 = ((uint64_t)sd.t0_hi << 32 | sd.t0_lo) + (uint64_t)s;
+  A.t_lo = (uint32_t)t0;
+  A.t_hi = (uint32_t)(t0 >> 32);
+  A.key0 = d.key0;
+  A.key1 = d.key1;
+  const PhiloxKey ks = philox_schedule(A.key0, A.key1);
+  const int32_t lt = bid - d.tile0;
+  const int32_t tx = lt % d.gx, ty = lt / d.gx;
+  const int32_t cx = (int32_t)tid % d.CX, rg = (int32_t)tid / d.CX;
+  const int32_t chunk = tx * d.CX + cx;
+  const int32_t i0 = (ty * d.RG + rg) * d.TR;
+  uint32_t ne = 0, rows = 0;
+  if (rg < d.RG && chunk * 16 < d.H && i0 < d.L) {
+    rows = (uint32_t)min(d.TR, d.L - i0);
+    const uint8_t *tab = reinterpret_cast<const uint8_t *>(s_tab);
+    uint32_t *lh = s_hist + (tid & 31u);
+    const int32_t x0 = chunk * 16;
+    switch (d.qbits) {
+      case 4:
+        walk_column<4, COLOUR, COUNTS, false, LT0>(A, ks, tab, x0, i0,
+                                                   (int)rows, lh, &ne);
+        break;
+      case 5:
+        walk_column<5, COLOUR, COUNTS, false, LT0>(A, ks, tab, x0, i0,
+                                                   (int)rows, lh, &ne);
+        break;
+      default:
+        // q > 32: the exact byte test serves every q <= 256
+        walk_column<8, COLOUR, COUNTS, false, LT0>(A, ks, tab, x0, i0,
+                                                   (int)rows, lh, &ne);
+        break;
     }
-    unsigned long long *rec = d.rec + (int64_t)s * (1 + d.q);
-    if (COUNTS) {
-      uint32_t sat = 64u * rows - ne;
+  }
+  unsigned long long *rec = sd.rec + (int64_t)s * (1 + d.q);
+  if (COUNTS) {
+    uint32_t sat = 64u * rows - ne;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-        sat += __shfl_xor_sync(0xFFFFFFFFu, sat, o);
-      if ((tid & 31u) == 0 && sat) atomicAdd(&s_sat, sat);
-    }
-    __syncthreads();
-    if (COUNTS && tid == 0 && s_sat) atomicAdd(rec, (unsigned long long)s_sat);
-    for (uint32_t v = tid; v < q; v += kPassThreads) {
-      uint32_t sum = 0;
+    for (int o = 16; o > 0; o >>= 1)
+      sat += __shfl_xor_sync(0xFFFFFFFFu, sat, o);
+    if ((tid & 31u) == 0 && sat) atomicAdd(&s_sat, sat);
+  }
+  __syncthreads();
+  if (COUNTS && tid == 0 && s_sat) atomicAdd(rec, (unsigned long long)s_sat);
+  for (uint32_t v = tid; v < q; v += kPassThreads) {
+    uint32_t sum = 0;
 #pragma unroll 8
-      for (int l = 0; l < 32; ++l) sum += s_hist[v * 32u + l];
-      if (sum) atomicAdd(rec + 1 + v, (unsigned long long)sum);
-    }
-    __syncthreads();
+    for (int l = 0; l < 32; ++l) sum += s_hist[v * 32u + l];
+    if (sum) atomicAdd(rec + 1 + v, (unsigned long long)sum);
   }
 }
 
-cudaError_t launch_batch_pass(const LatDesc *d_desc, const TileRef *d_tiles,
-                              int32_t ntiles, int32_t colour, int32_t s,
-                              int32_t grid, size_t smem, cudaStream_t st) {
-  if (colour)
-    batch_pass_kernel<1><<<grid, kPassThreads, smem, st>>>(d_desc, d_tiles,
-                                                           ntiles, s);
-  else
-    batch_pass_kernel<0><<<grid, kPassThreads, smem, st>>>(d_desc, d_tiles,
-                                                           ntiles, s);
+cudaError_t launch_batch_pass(const LaunchParams &P, bool lt0,
+                              const StepDesc *d_step, int32_t colour,
+                              int32_t s, size_t smem, cudaStream_t st) {
+  if (P.ntiles <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)P.ntiles), block(kPassThreads);
+  if (colour) {
+    if (lt0) batch_pass_kernel<1, true><<<grid, block, smem, st>>>(P, d_step, s);
+    else batch_pass_kernel<1, false><<<grid, block, smem, st>>>(P, d_step, s);
+  } else {
+    if (lt0) batch_pass_kernel<0, true><<<grid, block, smem, st>>>(P, d_step, s);
+    else batch_pass_kernel<0, false><<<grid, block, smem, st>>>(P, d_step, s);
+  }
   return cudaGetLastError();
-}
-
-int batch_blocks_per_sm(size_t smem) {
-  int a = 0, b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &a, batch_pass_kernel<0>, kPassThreads, smem) != cudaSuccess)
-    a = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &b, batch_pass_kernel<1>, kPassThreads, smem) != cudaSuccess)
-    b = 1;
-  return std::max(1, std::min(a, b));
 }
 
 // ------------------------------------------------------------- engine
 Engine::~Engine() {
   drop_graph();
-  if (d_desc_) cudaFree(d_desc_);
-  if (h_desc_) cudaFreeHost(h_desc_);
-  if (d_tiles_) cudaFree(d_tiles_);
+  drop_units();
+  if (d_step_) cudaFree(d_step_);
+  if (h_step_) cudaFreeHost(h_step_);
   if (d_rec_) cudaFree(d_rec_);
   if (h_rec_) cudaFreeHost(h_rec_);
+  if (pool_) cudaMemPoolDestroy(pool_);
 }
 
 void Engine::drop_graph() {
@@ -143,9 +133,27 @@ void Engine::drop_graph() {
   graph_k_ = -1;
 }
 
+void Engine::drop_units() {
+  for (Unit &u : units_) delete u.P;
+  units_.clear();
+}
+
 int Engine::init(cudaStream_t stream) {
   st_ = stream;
   sm_count_ = sm_count_of_current_device();
+  // Lattice planes come from a pool owned by the engine: stream-ordered
+  // allocations that keep their memory between members, so admitting and
+  // retiring lattices does not synchronise the device.
+  int dev = 0;
+  POTTS_CK(cudaGetDevice(&dev));
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  POTTS_CK(cudaMemPoolCreate(&pool_, &props));
+  uint64_t keep = UINT64_MAX;
+  POTTS_CK(cudaMemPoolSetAttribute(pool_, cudaMemPoolAttrReleaseThreshold,
+                                   &keep));
   return POTTS_OK;
 }
 
@@ -155,11 +163,13 @@ size_t Engine::member_bytes(int32_t L) const {
 
 int Engine::create_member(Member *m) {
   m->plane_bytes = (int64_t)m->L * (m->L / 2);
-  cudaError_t e = cudaMalloc(&m->planes, (size_t)(2 * m->plane_bytes));
+  cudaError_t e = cudaMallocFromPoolAsync(
+      reinterpret_cast<void **>(&m->planes), (size_t)(2 * m->plane_bytes),
+      pool_, st_);
   if (e != cudaSuccess) {
     cudaGetLastError();
     m->planes = nullptr;
-    return fail(POTTS_ENOMEM, "cudaMalloc(%lld bytes) for a member: %s",
+    return fail(POTTS_ENOMEM, "allocation of %lld bytes for a member: %s",
                 (long long)(2 * m->plane_bytes), cudaGetErrorString(e));
   }
   m->owns_planes = true;
@@ -171,9 +181,10 @@ int Engine::create_member(Member *m) {
     POTTS_CK(launch_init_random(m->planes + m->plane_bytes, m->plane_bytes,
                                 (uint32_t)m->q, 1, m->seed, st_));
   }
-  // initial counts
+  if (!initial_counts) return POTTS_OK;
   unsigned long long *d = nullptr;
-  POTTS_CK(cudaMallocAsync(&d, (size_t)(1 + m->q) * 8, st_));
+  POTTS_CK(cudaMallocFromPoolAsync(reinterpret_cast<void **>(&d),
+                                   (size_t)(1 + m->q) * 8, pool_, st_));
   POTTS_CK(cudaMemsetAsync(d, 0, (size_t)(1 + m->q) * 8, st_));
   POTTS_CK(launch_recount(m->planes, m->planes + m->plane_bytes, m->L,
                           m->L / 2, (uint32_t)m->q, d, st_));
@@ -187,7 +198,7 @@ int Engine::create_member(Member *m) {
 }
 
 void Engine::free_member(Member *m) {
-  if (m->planes && m->owns_planes) cudaFree(m->planes);
+  if (m->planes && m->owns_planes) cudaFreeAsync(m->planes, st_);
   m->planes = nullptr;
 }
 
@@ -198,23 +209,21 @@ void Engine::set_members(const std::vector<Member *> &members) {
 
 int Engine::ensure_capacity(int32_t k) {
   const size_t n = members_.size();
-  if (n > desc_cap_) {
-    if (d_desc_) cudaFree(d_desc_);
-    if (h_desc_) cudaFreeHost(h_desc_);
-    d_desc_ = nullptr;
-    h_desc_ = nullptr;
-    const size_t cap = std::max<size_t>(n, 2 * desc_cap_);
-    POTTS_CK(cudaMalloc(&d_desc_, cap * sizeof(LatDesc)));
-    POTTS_CK(cudaMallocHost(&h_desc_, cap * sizeof(LatDesc)));
-    desc_cap_ = cap;
+  if (n > step_cap_) {
+    if (d_step_) cudaFree(d_step_);
+    if (h_step_) cudaFreeHost(h_step_);
+    d_step_ = nullptr;
+    h_step_ = nullptr;
+    const size_t cap = std::max<size_t>(n, 2 * step_cap_);
+    POTTS_CK(cudaMalloc(&d_step_, cap * sizeof(StepDesc)));
+    POTTS_CK(cudaMallocHost(&h_step_, cap * sizeof(StepDesc)));
+    step_cap_ = cap;
     dirty_ = true;
   }
   size_t need = 0;
-  int32_t maxq = 2;
   for (Member *m : members_) {
     m->rec_off = (int64_t)need;
     need += (size_t)k * (1 + m->q);
-    maxq = std::max(maxq, m->q);
   }
   rec_used_ = need;
   if (need > rec_cap_) {
@@ -228,50 +237,78 @@ int Engine::ensure_capacity(int32_t k) {
     rec_cap_ = cap;
     dirty_ = true;
   }
-  if (maxq != max_q_) dirty_ = true;
-  max_q_ = maxq;
+  // the acceptance rule picks the kernel: a change regroups the members
+  member_lt0_.resize(n);
+  for (size_t i = 0; i < n; ++i) {
+    uint64_t thr[5];
+    if (!threshold_table(members_[i]->beta, thr))
+      return fail(POTTS_EINVAL, "beta must be finite and >= 0 (got %g)",
+                  members_[i]->beta);
+    const uint8_t lt0 = accept_table(thr).rule_lt0 ? 1 : 0;
+    if (lt0 != member_lt0_[i]) dirty_ = true;
+    member_lt0_[i] = lt0;
+  }
   return POTTS_OK;
 }
 
-int Engine::rebuild(int32_t k) {
-  // tile list: per member, its row tiles (shape from choose_geom, with the
-  // tuned walk length as a cap)
-  std::vector<TileRef> tiles;
-  for (size_t i = 0; i < members_.size(); ++i) {
-    Member *m = members_[i];
-    const int32_t H = m->L / 2;
-    TileGeom g = choose_geom(m->L, H, m->q, sm_count_, m->TR);
-    LatDesc &d = h_desc_[i];
-    d.CX = g.CX;
-    d.RG = g.RG;
-    d.TR = g.TR;
-    const int32_t nchunks = H / 16;
-    for (int32_t ty = 0; ty < g.ty; ++ty)
-      for (int32_t tx = 0; tx * g.CX < nchunks; ++tx)
-        tiles.push_back(TileRef{(int32_t)i, tx * g.CX, ty * g.RG * g.TR, 0});
-  }
-  // big members first so the tail of the persistent loop is short tiles
-  std::stable_sort(tiles.begin(), tiles.end(),
-                   [&](const TileRef &a, const TileRef &b) {
-                     return members_[a.lat]->L > members_[b.lat]->L;
-                   });
-  ntiles_ = (int32_t)tiles.size();
-  if (tiles.size() > tiles_cap_) {
-    if (d_tiles_) cudaFree(d_tiles_);
-    d_tiles_ = nullptr;
-    POTTS_CK(cudaMalloc(&d_tiles_, tiles.size() * sizeof(TileRef)));
-    tiles_cap_ = tiles.size();
-  }
-  if (!tiles.empty())
-    POTTS_CK(cudaMemcpyAsync(d_tiles_, tiles.data(),
-                             tiles.size() * sizeof(TileRef),
-                             cudaMemcpyHostToDevice, st_));
-  smem_ = (size_t)max_q_ * 32 * sizeof(uint32_t);
-  const int bps = batch_blocks_per_sm(smem_);
-  grid_ = std::max(1, std::min<int32_t>(ntiles_, sm_count_ * bps));
+// Groups the members by acceptance rule into launches of at most
+// kMaxMembersPerLaunch members, biggest lattices first, and lays out their
+// row tiles (one CTA each).
+int Engine::rebuild() {
   drop_graph();
+  drop_units();
+  std::vector<size_t> order(members_.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+    return members_[a]->L > members_[b]->L;
+  });
+  for (int rule = 0; rule < 2; ++rule) {
+    Unit u;
+    for (size_t i : order) {
+      if (member_lt0_[i] != rule) continue;
+      if (!u.P || u.P->n == kMaxMembersPerLaunch) {
+        if (u.P) units_.push_back(u);
+        u = Unit();
+        u.P = new (std::nothrow) LaunchParams();
+        if (!u.P) return fail(POTTS_ENOMEM, "host allocation failed");
+        u.lt0 = rule == 1;
+      }
+      Member *m = members_[i];
+      const int32_t H = m->L / 2;
+      const TileGeom g = choose_geom(m->L, H, m->q, sm_count_, m->TR);
+      StaticDesc &d = u.P->m[u.P->n];
+      d.plane[0] = m->planes;
+      d.plane[1] = m->planes + m->plane_bytes;
+      d.L = m->L;
+      d.H = H;
+      d.q = m->q;
+      d.qbits = qbits_for(m->q);
+      d.key0 = (uint32_t)m->seed;
+      d.key1 = (uint32_t)(m->seed >> 32);
+      d.CX = g.CX;
+      d.RG = g.RG;
+      d.TR = g.TR;
+      d.gx = g.gx;
+      d.tile0 = u.P->ntiles;
+      d.step = (int32_t)i;
+      u.P->ntiles += g.gx * g.ty;
+      u.P->n += 1;
+      u.maxq = std::max(u.maxq, m->q);
+    }
+    if (u.P) units_.push_back(u);
+  }
   dirty_ = false;
-  (void)k;
+  return POTTS_OK;
+}
+
+int Engine::launch_all(int32_t kmax) {
+  POTTS_CK(cudaMemsetAsync(d_rec_, 0, rec_used_ * 8, st_));
+  for (int32_t s = 0; s < kmax; ++s)
+    for (int c = 0; c < 2; ++c)
+      for (const Unit &u : units_)
+        POTTS_CK(launch_batch_pass(*u.P, u.lt0, d_step_, c, s,
+                                   (size_t)u.maxq * 32 * sizeof(uint32_t),
+                                   st_));
   return POTTS_OK;
 }
 
@@ -279,18 +316,16 @@ int Engine::capture(int32_t k) {
   drop_graph();
   cudaGraph_t g = nullptr;
   POTTS_CK(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaMemsetAsync(d_rec_, 0, rec_used_ * 8, st_);
-  for (int32_t s = 0; s < k && e == cudaSuccess; ++s)
-    for (int c = 0; c < 2 && e == cudaSuccess; ++c)
-      e = launch_batch_pass(d_desc_, d_tiles_, ntiles_, c, s, grid_, smem_,
-                            st_);
+  const int rc = launch_all(k);
   cudaError_t e2 = cudaStreamEndCapture(st_, &g);
-  if (e != cudaSuccess || e2 != cudaSuccess) {
+  if (rc != POTTS_OK || e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
-    return fail(POTTS_ECUDA, "graph capture failed: %s",
-                cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return rc != POTTS_OK
+               ? rc
+               : fail(POTTS_ECUDA, "graph capture failed: %s",
+                      cudaGetErrorString(e2));
   }
-  e = cudaGraphInstantiate(&gexec_, g, 0);
+  cudaError_t e = cudaGraphInstantiate(&gexec_, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
     gexec_ = nullptr;
@@ -306,35 +341,25 @@ int Engine::step(int32_t k) {
   if (rc) return rc;
   const bool was_dirty = dirty_;
   if (dirty_) {
-    rc = rebuild(k);
+    rc = rebuild();
     if (rc) return rc;
   }
   int32_t kmax = 0;
   for (size_t i = 0; i < members_.size(); ++i) {
     Member *m = members_[i];
     uint64_t thr[5];
-    if (!threshold_table(m->beta, thr))
-      return fail(POTTS_EINVAL, "beta must be finite and >= 0 (got %g)",
-                  m->beta);
+    threshold_table(m->beta, thr);  // validated in ensure_capacity
     const AcceptTable T = accept_table(thr);
-    LatDesc &d = h_desc_[i];
-    d.plane[0] = m->planes;
-    d.plane[1] = m->planes + m->plane_bytes;
-    d.L = m->L;
-    d.H = m->L / 2;
-    d.q = m->q;
-    d.qbits = qbits_for(m->q);
-    d.key0 = (uint32_t)m->seed;
-    d.key1 = (uint32_t)(m->seed >> 32);
+    StepDesc &d = h_step_[i];
     d.t0_lo = (uint32_t)m->sweep;
     d.t0_hi = (uint32_t)(m->sweep >> 32);
     d.nsweeps = std::min(m->nsweeps_step, k);
-    d.rec = d_rec_ + m->rec_off;
     std::memcpy(d.tab, T.tab, sizeof d.tab);
-    d.lt0 = T.rule_lt0;
+    d.rec = d_rec_ + m->rec_off;
     kmax = std::max(kmax, d.nsweeps);
   }
-  POTTS_CK(cudaMemcpyAsync(d_desc_, h_desc_, members_.size() * sizeof(LatDesc),
+  POTTS_CK(cudaMemcpyAsync(d_step_, h_step_,
+                           members_.size() * sizeof(StepDesc),
                            cudaMemcpyHostToDevice, st_));
   if (kmax == k && !was_dirty) {
     // steady state: replay the captured step
@@ -344,18 +369,15 @@ int Engine::step(int32_t k) {
     }
     POTTS_CK(cudaGraphLaunch(gexec_, st_));
   } else {
-    POTTS_CK(cudaMemsetAsync(d_rec_, 0, rec_used_ * 8, st_));
-    for (int32_t s = 0; s < kmax; ++s)
-      for (int c = 0; c < 2; ++c)
-        POTTS_CK(launch_batch_pass(d_desc_, d_tiles_, ntiles_, c, s, grid_,
-                                   smem_, st_));
+    rc = launch_all(kmax);
+    if (rc) return rc;
   }
   POTTS_CK(cudaMemcpyAsync(h_rec_, d_rec_, rec_used_ * 8,
                            cudaMemcpyDeviceToHost, st_));
   POTTS_CK(cudaStreamSynchronize(st_));
   for (size_t i = 0; i < members_.size(); ++i) {
     Member *m = members_[i];
-    const int32_t n = h_desc_[i].nsweeps;
+    const int32_t n = h_step_[i].nsweeps;
     for (int32_t s = 0; s < n; ++s)
       update_obs(&m->obs, h_rec_ + m->rec_off + (int64_t)s * (1 + m->q), m->L,
                  m->q, true);
@@ -392,6 +414,7 @@ int Engine::autotune(int32_t max_k) {
   size_t total = 0;
   for (Member *m : members_) total += (size_t)(2 * m->plane_bytes);
   uint8_t *scratch = nullptr;
+  POTTS_CK(cudaStreamSynchronize(st_));
   if (cudaMalloc(&scratch, total) != cudaSuccess) {
     cudaGetLastError();
     return POTTS_OK;  // no room to tune: keep the defaults
@@ -472,7 +495,10 @@ struct potts_batch {
   bool tuned = false;
   ~potts_batch() {
     for (Member &m : members) eng.free_member(&m);
-    if (stream) cudaStreamDestroy(stream);
+    if (stream) {
+      cudaStreamSynchronize(stream);
+      cudaStreamDestroy(stream);
+    }
   }
 };
 
@@ -505,7 +531,11 @@ int potts_batch_create(int32_t n, const int32_t *L, const int32_t *q,
     delete b;
     return fail(POTTS_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
   }
-  b->eng.init(b->stream);
+  int rc0 = b->eng.init(b->stream);
+  if (rc0 != POTTS_OK) {
+    delete b;
+    return rc0;
+  }
   b->members.resize((size_t)n);
   std::vector<Member *> ptrs;
   for (int32_t i = 0; i < n; ++i) {

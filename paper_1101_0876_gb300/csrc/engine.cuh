@@ -1,9 +1,10 @@
 // Batched sweep engine: many independent lattices of different L, q, beta
 // and seed advanced together.  Each colour pass of every member runs in one
-// persistent launch over a flat (lattice, row tile) work list; a step of k
-// sweeps (2k launches plus the zeroing of the step's records) is captured
-// in one CUDA graph and replayed while the membership does not change.
-// Used by the batch API and by the serving loop.
+// launch with one CTA per row tile of every member (members are found from
+// the CTA index through the launch's parameter block); a step of k sweeps
+// (2k launches plus the zeroing of the step's records) is captured in one
+// CUDA graph and replayed while the membership does not change.  Used by
+// the batch API and by the serving loop.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -14,24 +15,36 @@
 
 namespace potts {
 
-// Device descriptor of one member for the current step.
-struct LatDesc {
+// Per-member data that stays fixed while the membership does not change.
+// A launch carries up to kMaxMembersPerLaunch of them in its parameter block
+// (constant bank), so every field is a uniform operand inside the kernel.
+struct StaticDesc {
   uint8_t *plane[2];          // white, black
   int32_t L, H, q, qbits;
-  uint32_t key0, key1;
-  uint32_t t0_lo, t0_hi;      // global index of the step's first sweep
-  int32_t nsweeps;            // sweeps of this member in this step (<= k)
-  int32_t CX, RG, TR;         // row-tile shape
-  unsigned long long *rec;    // [k][1 + q] records of this step
-  uint32_t tab[9];            // acceptance table (see AcceptTable)
-  uint32_t lt0;
+  uint32_t key0, key1;        // seed
+  int32_t CX, RG, TR, gx;     // row-tile shape; gx tiles per row band
+  int32_t tile0;              // first tile (CTA) of this member in the launch
+  int32_t step;               // index of its StepDesc
 };
 
-struct TileRef {
-  int32_t lat;   // member index
-  int32_t cx0;   // first 16-byte chunk of the tile
-  int32_t i0;    // first row of the tile
-  int32_t pad;
+// Per-member data that changes every step (device array).
+struct StepDesc {
+  uint32_t t0_lo, t0_hi;      // global index of the step's first sweep
+  int32_t nsweeps;            // sweeps of this member in this step (<= k)
+  uint32_t pad0;
+  uint32_t tab[9];            // acceptance table (see AcceptTable)
+  uint32_t pad1[3];
+  unsigned long long *rec;    // [k][1 + q] records of this step
+  unsigned long long pad2;
+};
+
+constexpr int kMaxMembersPerLaunch = 440;
+
+struct LaunchParams {
+  int32_t n;        // members in this launch
+  int32_t ntiles;   // CTAs of this launch
+  int32_t pad[2];
+  StaticDesc m[kMaxMembersPerLaunch];
 };
 
 // Host-side state of one member.
@@ -80,37 +93,43 @@ class Engine {
   int copy_spins(const Member *m, uint8_t *out_LxL);
   size_t member_bytes(int32_t L) const;
 
+  // Serving members skip the initial recount (their records come from the
+  // sweeps), so admission does not wait for the device.
+  bool initial_counts = true;
+
  private:
+  struct Unit {               // one launch: members sharing a rule
+    LaunchParams *P = nullptr;
+    bool lt0 = false;
+    int32_t maxq = 2;
+  };
   int ensure_capacity(int32_t k);
-  int rebuild(int32_t k);
+  int rebuild();
+  int launch_all(int32_t kmax);
   int capture(int32_t k);
   void drop_graph();
+  void drop_units();
 
   cudaStream_t st_ = nullptr;
+  cudaMemPool_t pool_ = nullptr;
   int sm_count_ = 1;
   std::vector<Member *> members_;
+  std::vector<uint8_t> member_lt0_;
   bool dirty_ = true;
   int32_t graph_k_ = -1;
   cudaGraphExec_t gexec_ = nullptr;
-  LatDesc *d_desc_ = nullptr, *h_desc_ = nullptr;
-  size_t desc_cap_ = 0;
-  TileRef *d_tiles_ = nullptr;
-  size_t tiles_cap_ = 0;
-  int32_t ntiles_ = 0;
+  std::vector<Unit> units_;
+  StepDesc *d_step_ = nullptr, *h_step_ = nullptr;
+  size_t step_cap_ = 0;
   unsigned long long *d_rec_ = nullptr;
   uint64_t *h_rec_ = nullptr;
   size_t rec_cap_ = 0, rec_used_ = 0;
-  int32_t max_q_ = 2;
-  int32_t grid_ = 1;
-  size_t smem_ = 0;
   int32_t tuned_k_ = 16, tuned_tr_ = 0;
-  unsigned long long *d_scratch_rec_ = nullptr;
 };
 
-// Launch of one batched colour pass (all members, sweep offset s).
-cudaError_t launch_batch_pass(const LatDesc *d_desc, const TileRef *d_tiles,
-                              int32_t ntiles, int32_t colour, int32_t s,
-                              int32_t grid, size_t smem, cudaStream_t st);
-int batch_blocks_per_sm(size_t smem);
+// One batched colour pass of the members of P at sweep offset s.
+cudaError_t launch_batch_pass(const LaunchParams &P, bool lt0,
+                              const StepDesc *d_step, int32_t colour,
+                              int32_t s, size_t smem, cudaStream_t st);
 
 }  // namespace potts

@@ -199,7 +199,13 @@ int potts_serve_start(const potts_serve_cfg *cfg, potts_server_h *out) {
     delete s;
     return fail(POTTS_ECUDA, "server stream: %s", cudaGetErrorString(e));
   }
-  s->eng.init(s->st);
+  int rc = s->eng.init(s->st);
+  if (rc != POTTS_OK) {
+    cudaStreamDestroy(s->st);
+    delete s;
+    return rc;
+  }
+  s->eng.initial_counts = false;
   try {
     s->th = std::thread([s] { s->run(); });
   } catch (...) {

@@ -175,3 +175,31 @@ def test_paper_scale_sampled(q, t_over_tc):
 def test_q96_L16384_sampled():
     cfg = workloads.PAPER_Q96
     _sampled_sweep_parity(cfg.L, cfg.q, cfg.start, cfg.seed, 1.005, warm=2)
+
+
+# ------------------------------------------------------------ mid config
+@pytest.mark.parametrize("start,ladder_dir", [(0, 1), (1, -1)])
+def test_mid_config_protocol(start, ladder_dir):
+    """L=4096, q=9, seed 7: heating from the ordered start (T ascending) and
+    cooling from the random start (T descending) over the ladder in
+    [0.97, 1.03] T_c.  The first two temperatures (2 sweeps each) are
+    compared with the oracle in full; after 3 x 40 more sweeps one sweep is
+    compared on sampled sites."""
+    L, q, seed = workloads.MID["L"], workloads.MID["q"], workloads.MID["seed"]
+    ladder = list(workloads.MID["ladder"])[::ladder_dir]
+    g = potts.Lattice(L, q, start, seed)
+    o = oracle.Lattice(L, q, start, seed)
+    for t in ladder[:2]:
+        b = workloads.beta_at(q, t)
+        assert np.array_equal(g.sweep(b, 2), o.sweep(b, 2)), t
+    assert np.array_equal(g.spins(), o.spins())
+    for t in ladder[2:5]:
+        g.sweep(workloads.beta_at(q, t), 40, records=False)
+    b = workloads.beta_at(q, ladder[5])
+    pre, tidx = g.spins(), g.sweep_index
+    rec = g.sweep(b, 1)
+    idx = np.random.default_rng(5).integers(0, L * L, 200_000, dtype=np.int64)
+    assert np.array_equal(g.spins().ravel()[idx],
+                          oracle.sweep_sites(pre, q, seed, tidx, b, idx))
+    B, hist = oracle.recount(g.spins(), q)
+    assert int(rec[0, 0]) == B and np.array_equal(rec[0, 1:], hist)
