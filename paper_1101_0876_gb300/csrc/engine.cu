@@ -14,6 +14,8 @@ namespace potts {
 // walk, Philox counters and reductions of the single-lattice pass on that
 // tile, into the member's record of sweep s.  Members whose step has fewer
 // than s+1 sweeps return at once.
+constexpr int32_t kEngineTR = 32;
+
 #ifndef POTTS_BATCH_MINB
 #define POTTS_BATCH_MINB 4
 #endif
@@ -117,20 +119,30 @@ cudaError_t launch_batch_pass(const LaunchParams &P, bool lt0,
 }
 
 // ------------------------------------------------------------- engine
-Engine::~Engine() {
-  drop_graph();
-  drop_units();
-  if (d_step_) cudaFree(d_step_);
-  if (h_step_) cudaFreeHost(h_step_);
-  if (d_rec_) cudaFree(d_rec_);
-  if (h_rec_) cudaFreeHost(h_rec_);
-  if (pool_) cudaMemPoolDestroy(pool_);
-}
+Engine::~Engine() { release(); }
 
-void Engine::drop_graph() {
-  if (gexec_) cudaGraphExecDestroy(gexec_);
-  gexec_ = nullptr;
-  graph_k_ = -1;
+void Engine::release() {
+  if (st_) cudaStreamSynchronize(st_);
+  st_ = nullptr;
+  inflight_.clear();
+  for (Slot &sl : slots_) {
+    if (sl.gexec) cudaGraphExecDestroy(sl.gexec);
+    if (sl.d_step) cudaFree(sl.d_step);
+    if (sl.h_step) cudaFreeHost(sl.h_step);
+    if (sl.d_rec) cudaFree(sl.d_rec);
+    if (sl.h_rec) cudaFreeHost(sl.h_rec);
+    if (sl.done) cudaEventDestroy(sl.done);
+    sl = Slot();
+  }
+  drop_units();
+  if (aux_) cudaStreamSynchronize(aux_);
+  if (aux_) cudaStreamDestroy(aux_);
+  if (fork_) cudaEventDestroy(fork_);
+  if (join_) cudaEventDestroy(join_);
+  aux_ = nullptr;
+  fork_ = join_ = nullptr;
+  if (pool_) cudaMemPoolDestroy(pool_);
+  pool_ = nullptr;
 }
 
 void Engine::drop_units() {
@@ -154,11 +166,12 @@ int Engine::init(cudaStream_t stream) {
   uint64_t keep = UINT64_MAX;
   POTTS_CK(cudaMemPoolSetAttribute(pool_, cudaMemPoolAttrReleaseThreshold,
                                    &keep));
+  for (Slot &sl : slots_)
+    POTTS_CK(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+  POTTS_CK(cudaStreamCreateWithFlags(&aux_, cudaStreamNonBlocking));
+  POTTS_CK(cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming));
+  POTTS_CK(cudaEventCreateWithFlags(&join_, cudaEventDisableTiming));
   return POTTS_OK;
-}
-
-size_t Engine::member_bytes(int32_t L) const {
-  return (size_t)L * (size_t)(L / 2) * 2;
 }
 
 int Engine::create_member(Member *m) {
@@ -173,6 +186,7 @@ int Engine::create_member(Member *m) {
                 (long long)(2 * m->plane_bytes), cudaGetErrorString(e));
   }
   m->owns_planes = true;
+  m->sweep_next = m->sweep;
   if (m->start == POTTS_START_ORDERED) {
     POTTS_CK(cudaMemsetAsync(m->planes, 0, (size_t)(2 * m->plane_bytes), st_));
   } else {
@@ -207,46 +221,32 @@ void Engine::set_members(const std::vector<Member *> &members) {
   dirty_ = true;
 }
 
-int Engine::ensure_capacity(int32_t k) {
+int Engine::slot_capacity(Slot &sl, int32_t k) {
   const size_t n = members_.size();
-  if (n > step_cap_) {
-    if (d_step_) cudaFree(d_step_);
-    if (h_step_) cudaFreeHost(h_step_);
-    d_step_ = nullptr;
-    h_step_ = nullptr;
-    const size_t cap = std::max<size_t>(n, 2 * step_cap_);
-    POTTS_CK(cudaMalloc(&d_step_, cap * sizeof(StepDesc)));
-    POTTS_CK(cudaMallocHost(&h_step_, cap * sizeof(StepDesc)));
-    step_cap_ = cap;
-    dirty_ = true;
+  if (n > sl.step_cap) {
+    if (sl.d_step) cudaFree(sl.d_step);
+    if (sl.h_step) cudaFreeHost(sl.h_step);
+    sl.d_step = nullptr;
+    sl.h_step = nullptr;
+    const size_t cap = std::max<size_t>(n, 2 * sl.step_cap);
+    POTTS_CK(cudaMalloc(&sl.d_step, cap * sizeof(StepDesc)));
+    POTTS_CK(cudaMallocHost(&sl.h_step, cap * sizeof(StepDesc)));
+    sl.step_cap = cap;
+    sl.graph_gen = 0;
   }
   size_t need = 0;
-  for (Member *m : members_) {
-    m->rec_off = (int64_t)need;
-    need += (size_t)k * (1 + m->q);
-  }
-  rec_used_ = need;
-  if (need > rec_cap_) {
-    if (d_rec_) cudaFree(d_rec_);
-    if (h_rec_) cudaFreeHost(h_rec_);
-    d_rec_ = nullptr;
-    h_rec_ = nullptr;
-    const size_t cap = std::max(need, 2 * rec_cap_);
-    POTTS_CK(cudaMalloc(&d_rec_, cap * 8));
-    POTTS_CK(cudaMallocHost(&h_rec_, cap * 8));
-    rec_cap_ = cap;
-    dirty_ = true;
-  }
-  // the acceptance rule picks the kernel: a change regroups the members
-  member_lt0_.resize(n);
-  for (size_t i = 0; i < n; ++i) {
-    uint64_t thr[5];
-    if (!threshold_table(members_[i]->beta, thr))
-      return fail(POTTS_EINVAL, "beta must be finite and >= 0 (got %g)",
-                  members_[i]->beta);
-    const uint8_t lt0 = accept_table(thr).rule_lt0 ? 1 : 0;
-    if (lt0 != member_lt0_[i]) dirty_ = true;
-    member_lt0_[i] = lt0;
+  for (Member *m : members_) need += (size_t)k * (1 + m->q);
+  sl.rec_used = need;
+  if (need > sl.rec_cap) {
+    if (sl.d_rec) cudaFree(sl.d_rec);
+    if (sl.h_rec) cudaFreeHost(sl.h_rec);
+    sl.d_rec = nullptr;
+    sl.h_rec = nullptr;
+    const size_t cap = std::max(need, 2 * sl.rec_cap);
+    POTTS_CK(cudaMalloc(&sl.d_rec, cap * 8));
+    POTTS_CK(cudaMallocHost(&sl.h_rec, cap * 8));
+    sl.rec_cap = cap;
+    sl.graph_gen = 0;
   }
   return POTTS_OK;
 }
@@ -254,69 +254,100 @@ int Engine::ensure_capacity(int32_t k) {
 // Groups the members by acceptance rule into launches of at most
 // kMaxMembersPerLaunch members, biggest lattices first, and lays out their
 // row tiles (one CTA each).
+// Splits the members into two lanes of about equal work (sites), biggest
+// lattices first, and each lane by acceptance rule into launches of at most
+// kMaxMembersPerLaunch members; lays out their row tiles (one CTA each).
+// The lanes run on two streams, so the tail of one lane's pass overlaps
+// the other lane's work.
 int Engine::rebuild() {
-  drop_graph();
   drop_units();
   std::vector<size_t> order(members_.size());
   for (size_t i = 0; i < order.size(); ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
     return members_[a]->L > members_[b]->L;
   });
-  for (int rule = 0; rule < 2; ++rule) {
-    Unit u;
-    for (size_t i : order) {
-      if (member_lt0_[i] != rule) continue;
-      if (!u.P || u.P->n == kMaxMembersPerLaunch) {
-        if (u.P) units_.push_back(u);
-        u = Unit();
-        u.P = new (std::nothrow) LaunchParams();
-        if (!u.P) return fail(POTTS_ENOMEM, "host allocation failed");
-        u.lt0 = rule == 1;
+  lanes_ = members_.size() >= 2 ? 2 : 1;
+  std::vector<int> lane_of(members_.size(), 0);
+  double work[2] = {0, 0};
+  for (size_t i : order) {
+    const int l = (lanes_ == 2 && work[1] < work[0]) ? 1 : 0;
+    lane_of[i] = l;
+    work[l] += (double)members_[i]->L * members_[i]->L;
+  }
+  for (int lane = 0; lane < lanes_; ++lane) {
+    for (int rule = 0; rule < 2; ++rule) {
+      Unit u;
+      for (size_t i : order) {
+        if (member_lt0_[i] != rule || lane_of[i] != lane) continue;
+        if (!u.P || u.P->n == kMaxMembersPerLaunch) {
+          if (u.P) units_.push_back(u);
+          u = Unit();
+          u.P = new (std::nothrow) LaunchParams();
+          if (!u.P) return fail(POTTS_ENOMEM, "host allocation failed");
+          u.lt0 = rule == 1;
+          u.lane = lane;
+        }
+        Member *m = members_[i];
+        const int32_t H = m->L / 2;
+        // walks of kEngineTR rows by default: many lattices share the
+        // device, so each tile should carry enough sites to amortise its
+        // histogram set-up instead of spreading one lattice over every SM
+        const TileGeom g = choose_geom(m->L, H, m->q, sm_count_,
+                                       m->TR > 0 ? m->TR : kEngineTR);
+        StaticDesc &d = u.P->m[u.P->n];
+        d.plane[0] = m->planes;
+        d.plane[1] = m->planes + m->plane_bytes;
+        d.L = m->L;
+        d.H = H;
+        d.q = m->q;
+        d.qbits = qbits_for(m->q);
+        d.key0 = (uint32_t)m->seed;
+        d.key1 = (uint32_t)(m->seed >> 32);
+        d.CX = g.CX;
+        d.RG = g.RG;
+        d.TR = g.TR;
+        d.gx = g.gx;
+        d.tile0 = u.P->ntiles;
+        d.step = (int32_t)i;
+        u.P->ntiles += g.gx * g.ty;
+        u.P->n += 1;
+        u.maxq = std::max(u.maxq, m->q);
       }
-      Member *m = members_[i];
-      const int32_t H = m->L / 2;
-      const TileGeom g = choose_geom(m->L, H, m->q, sm_count_, m->TR);
-      StaticDesc &d = u.P->m[u.P->n];
-      d.plane[0] = m->planes;
-      d.plane[1] = m->planes + m->plane_bytes;
-      d.L = m->L;
-      d.H = H;
-      d.q = m->q;
-      d.qbits = qbits_for(m->q);
-      d.key0 = (uint32_t)m->seed;
-      d.key1 = (uint32_t)(m->seed >> 32);
-      d.CX = g.CX;
-      d.RG = g.RG;
-      d.TR = g.TR;
-      d.gx = g.gx;
-      d.tile0 = u.P->ntiles;
-      d.step = (int32_t)i;
-      u.P->ntiles += g.gx * g.ty;
-      u.P->n += 1;
-      u.maxq = std::max(u.maxq, m->q);
+      if (u.P) units_.push_back(u);
     }
-    if (u.P) units_.push_back(u);
   }
   dirty_ = false;
+  gen_ += 1;
+  stable_ = 0;
   return POTTS_OK;
 }
 
-int Engine::launch_all(int32_t kmax) {
-  POTTS_CK(cudaMemsetAsync(d_rec_, 0, rec_used_ * 8, st_));
+int Engine::launch_all(Slot &sl, int32_t kmax) {
+  POTTS_CK(cudaMemsetAsync(sl.d_rec, 0, sl.rec_used * 8, st_));
+  if (lanes_ == 2) {  // fork the second lane
+    POTTS_CK(cudaEventRecord(fork_, st_));
+    POTTS_CK(cudaStreamWaitEvent(aux_, fork_, 0));
+  }
   for (int32_t s = 0; s < kmax; ++s)
     for (int c = 0; c < 2; ++c)
       for (const Unit &u : units_)
-        POTTS_CK(launch_batch_pass(*u.P, u.lt0, d_step_, c, s,
+        POTTS_CK(launch_batch_pass(*u.P, u.lt0, sl.d_step, c, s,
                                    (size_t)u.maxq * 32 * sizeof(uint32_t),
-                                   st_));
+                                   u.lane ? aux_ : st_));
+  if (lanes_ == 2) {  // join
+    POTTS_CK(cudaEventRecord(join_, aux_));
+    POTTS_CK(cudaStreamWaitEvent(st_, join_, 0));
+  }
   return POTTS_OK;
 }
 
-int Engine::capture(int32_t k) {
-  drop_graph();
+int Engine::capture(Slot &sl, int32_t k) {
+  if (sl.gexec) cudaGraphExecDestroy(sl.gexec);
+  sl.gexec = nullptr;
+  sl.graph_gen = 0;
   cudaGraph_t g = nullptr;
   POTTS_CK(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
-  const int rc = launch_all(k);
+  const int rc = launch_all(sl, k);
   cudaError_t e2 = cudaStreamEndCapture(st_, &g);
   if (rc != POTTS_OK || e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -325,64 +356,125 @@ int Engine::capture(int32_t k) {
                : fail(POTTS_ECUDA, "graph capture failed: %s",
                       cudaGetErrorString(e2));
   }
-  cudaError_t e = cudaGraphInstantiate(&gexec_, g, 0);
+  cudaError_t e = cudaGraphInstantiate(&sl.gexec, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    gexec_ = nullptr;
+    sl.gexec = nullptr;
     return fail(POTTS_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
   }
-  graph_k_ = k;
+  sl.graph_k = k;
+  sl.graph_gen = gen_;
+  return POTTS_OK;
+}
+
+int Engine::launch(int32_t k) {
+  if (k <= 0) return POTTS_OK;
+  if ((int)inflight_.size() == 2) {
+    const int rc = complete();
+    if (rc) return rc;
+  }
+  const size_t n = members_.size();
+  // the acceptance rule picks the kernel: a change regroups the members
+  member_lt0_.resize(n);
+  std::vector<AcceptTable> tabs(n);
+  for (size_t i = 0; i < n; ++i) {
+    uint64_t thr[5];
+    if (!threshold_table(members_[i]->beta, thr))
+      return fail(POTTS_EINVAL, "beta must be finite and >= 0 (got %g)",
+                  members_[i]->beta);
+    tabs[i] = accept_table(thr);
+    const uint8_t lt0 = tabs[i].rule_lt0 ? 1 : 0;
+    if (lt0 != member_lt0_[i]) dirty_ = true;
+    member_lt0_[i] = lt0;
+  }
+  if (dirty_) {
+    const int rc = rebuild();
+    if (rc) return rc;
+  }
+  const int si = next_slot_;
+  next_slot_ ^= 1;
+  Slot &sl = slots_[si];
+  int rc = slot_capacity(sl, k);
+  if (rc) return rc;
+  StepRecords &r = sl.rec;
+  r.mem = members_;
+  r.nsw.assign(n, 0);
+  r.off.assign(n, 0);
+  int32_t kmax = 0;
+  int64_t off = 0;
+  for (size_t i = 0; i < n; ++i) {
+    Member *m = members_[i];
+    StepDesc &d = sl.h_step[i];
+    d.t0_lo = (uint32_t)m->sweep_next;
+    d.t0_hi = (uint32_t)(m->sweep_next >> 32);
+    d.nsweeps = std::max(0, std::min(m->nsweeps_step, k));
+    std::memcpy(d.tab, tabs[i].tab, sizeof d.tab);
+    d.rec = sl.d_rec + off;
+    r.nsw[i] = d.nsweeps;
+    r.off[i] = off;
+    off += (int64_t)k * (1 + m->q);
+    m->sweep_next += (uint64_t)d.nsweeps;
+    kmax = std::max(kmax, d.nsweeps);
+  }
+  r.base = sl.h_rec;
+  if (n) {
+    POTTS_CK(cudaMemcpyAsync(sl.d_step, sl.h_step, n * sizeof(StepDesc),
+                             cudaMemcpyHostToDevice, st_));
+  }
+  if (kmax > 0) {
+    if (kmax == k && stable_ > 0) {
+      // steady membership: replay this slot's captured step
+      if (!sl.gexec || sl.graph_k != k || sl.graph_gen != gen_) {
+        rc = capture(sl, k);
+        if (rc) return rc;
+      }
+      POTTS_CK(cudaGraphLaunch(sl.gexec, st_));
+    } else {
+      rc = launch_all(sl, kmax);
+      if (rc) return rc;
+    }
+    POTTS_CK(cudaMemcpyAsync(sl.h_rec, sl.d_rec, sl.rec_used * 8,
+                             cudaMemcpyDeviceToHost, st_));
+  }
+  POTTS_CK(cudaEventRecord(sl.done, st_));
+  stable_ += 1;
+  inflight_.push_back(si);
+  return POTTS_OK;
+}
+
+int Engine::complete() {
+  if (inflight_.empty()) return POTTS_OK;
+  const int si = inflight_.front();
+  inflight_.erase(inflight_.begin());
+  Slot &sl = slots_[si];
+  POTTS_CK(cudaEventSynchronize(sl.done));
+  const StepRecords &r = sl.rec;
+  for (size_t i = 0; i < r.mem.size(); ++i) {
+    Member *m = r.mem[i];
+    for (int32_t s = 0; s < r.nsw[i]; ++s)
+      update_obs(&m->obs, r.base + r.off[i] + (int64_t)s * (1 + m->q), m->L,
+                 m->q, true);
+    m->sweep += (uint64_t)r.nsw[i];
+    m->obs.sweep = m->sweep;
+  }
+  last_ = r;
   return POTTS_OK;
 }
 
 int Engine::step(int32_t k) {
-  if (members_.empty() || k <= 0) return POTTS_OK;
-  int rc = ensure_capacity(k);
+  int rc = launch(k);
   if (rc) return rc;
-  const bool was_dirty = dirty_;
-  if (dirty_) {
-    rc = rebuild();
+  while (!inflight_.empty()) {
+    rc = complete();
     if (rc) return rc;
   }
-  int32_t kmax = 0;
-  for (size_t i = 0; i < members_.size(); ++i) {
-    Member *m = members_[i];
-    uint64_t thr[5];
-    threshold_table(m->beta, thr);  // validated in ensure_capacity
-    const AcceptTable T = accept_table(thr);
-    StepDesc &d = h_step_[i];
-    d.t0_lo = (uint32_t)m->sweep;
-    d.t0_hi = (uint32_t)(m->sweep >> 32);
-    d.nsweeps = std::min(m->nsweeps_step, k);
-    std::memcpy(d.tab, T.tab, sizeof d.tab);
-    d.rec = d_rec_ + m->rec_off;
-    kmax = std::max(kmax, d.nsweeps);
-  }
-  POTTS_CK(cudaMemcpyAsync(d_step_, h_step_,
-                           members_.size() * sizeof(StepDesc),
-                           cudaMemcpyHostToDevice, st_));
-  if (kmax == k && !was_dirty) {
-    // steady state: replay the captured step
-    if (!gexec_ || graph_k_ != k) {
-      rc = capture(k);
-      if (rc) return rc;
-    }
-    POTTS_CK(cudaGraphLaunch(gexec_, st_));
-  } else {
-    rc = launch_all(kmax);
+  return POTTS_OK;
+}
+
+int Engine::drain() {
+  while (!inflight_.empty()) {
+    const int rc = complete();
     if (rc) return rc;
-  }
-  POTTS_CK(cudaMemcpyAsync(h_rec_, d_rec_, rec_used_ * 8,
-                           cudaMemcpyDeviceToHost, st_));
-  POTTS_CK(cudaStreamSynchronize(st_));
-  for (size_t i = 0; i < members_.size(); ++i) {
-    Member *m = members_[i];
-    const int32_t n = h_step_[i].nsweeps;
-    for (int32_t s = 0; s < n; ++s)
-      update_obs(&m->obs, h_rec_ + m->rec_off + (int64_t)s * (1 + m->q), m->L,
-                 m->q, true);
-    m->sweep += (uint64_t)n;
-    m->obs.sweep = m->sweep;
   }
   return POTTS_OK;
 }
@@ -407,6 +499,8 @@ int Engine::copy_spins(const Member *m, uint8_t *out_LxL) {
 // results.
 int Engine::autotune(int32_t max_k) {
   if (members_.empty()) return POTTS_OK;
+  int rc0 = drain();
+  if (rc0) return rc0;
   std::vector<uint8_t *> saved(members_.size(), nullptr);
   std::vector<uint64_t> sweeps(members_.size());
   std::vector<potts_obs> obs(members_.size());
@@ -428,14 +522,15 @@ int Engine::autotune(int32_t max_k) {
                              cudaMemcpyDeviceToDevice, st_));
     sweeps[i] = m->sweep;
     obs[i] = m->obs;
+    (void)0;
     nst[i] = m->nsweeps_step;
     trs[i] = m->TR;
   }
   cudaEvent_t e0, e1;
   POTTS_CK(cudaEventCreate(&e0));
   POTTS_CK(cudaEventCreate(&e1));
-  const int32_t trc[] = {0, 4, 8, 16, 32};
-  const int32_t kc[] = {1, 4, 16, 64};
+  const int32_t trc[] = {2, 8, 32, 64};
+  const int32_t kc[] = {4, 16, 64};
   float best = 1e30f;
   int32_t best_tr = 0, best_k = std::min<int32_t>(16, max_k);
   int rc = POTTS_OK;
@@ -471,12 +566,14 @@ int Engine::autotune(int32_t max_k) {
     cudaMemcpyAsync(m->planes, saved[i], (size_t)(2 * m->plane_bytes),
                     cudaMemcpyDeviceToDevice, st_);
     m->sweep = sweeps[i];
+    m->sweep_next = sweeps[i];
     m->obs = obs[i];
     m->nsweeps_step = nst[i];
     m->TR = best_tr;
   }
   cudaStreamSynchronize(st_);
   cudaFree(scratch);
+  last_ = StepRecords();
   tuned_tr_ = best_tr;
   tuned_k_ = best_k;
   dirty_ = true;
@@ -495,10 +592,8 @@ struct potts_batch {
   bool tuned = false;
   ~potts_batch() {
     for (Member &m : members) eng.free_member(&m);
-    if (stream) {
-      cudaStreamSynchronize(stream);
-      cudaStreamDestroy(stream);
-    }
+    eng.release();  // uses the stream: before it is destroyed
+    if (stream) cudaStreamDestroy(stream);
   }
 };
 
@@ -574,18 +669,31 @@ int potts_batch_sweep(potts_batch_h b, const double *beta, int64_t nsweeps,
     b->tuned = true;
   }
   const int32_t k = std::max<int32_t>(1, b->eng.tuned_k());
-  int64_t done = 0;
+  // two steps in flight: the host copies one step's records while the
+  // device runs the next
+  int64_t launched = 0, done = 0;
+  std::vector<int32_t> chunk;
   while (done < nsweeps) {
-    const int32_t n = (int32_t)std::min<int64_t>(k, nsweeps - done);
-    for (Member &m : b->members) m.nsweeps_step = n;
-    int rc = b->eng.step(k);
+    while (launched < nsweeps && b->eng.in_flight() < 2) {
+      const int32_t n = (int32_t)std::min<int64_t>(k, nsweeps - launched);
+      for (Member &m : b->members) m.nsweeps_step = n;
+      int rc = b->eng.launch(k);
+      if (rc) return rc;
+      chunk.push_back(n);
+      launched += n;
+    }
+    int rc = b->eng.complete();
     if (rc) return rc;
+    const int32_t n = chunk.front();
+    chunk.erase(chunk.begin());
     if (out_counts) {
-      for (size_t i = 0; i < b->members.size(); ++i) {
-        if (!out_counts[i]) continue;
-        const Member &m = b->members[i];
-        std::memcpy(out_counts[i] + done * (1 + m.q), b->eng.records(&m),
-                    (size_t)n * (1 + m.q) * 8);
+      const StepRecords &r = b->eng.last();
+      for (size_t i = 0; i < r.mem.size(); ++i) {
+        const Member *m = r.mem[i];
+        const size_t idx = (size_t)(m - b->members.data());
+        if (!out_counts[idx]) continue;
+        std::memcpy(out_counts[idx] + done * (1 + m->q), r.base + r.off[i],
+                    (size_t)n * (1 + m->q) * 8);
       }
     }
     done += n;

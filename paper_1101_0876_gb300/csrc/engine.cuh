@@ -51,38 +51,59 @@ struct LaunchParams {
 struct Member {
   int32_t L = 0, q = 0, start = 0;
   uint64_t seed = 0;
-  uint64_t sweep = 0;         // next global sweep index
+  uint64_t sweep = 0;         // sweeps whose records have been applied
+  uint64_t sweep_next = 0;    // sweeps launched (>= sweep)
   double beta = 0.0;
   uint8_t *planes = nullptr;  // device: white plane then black plane
   int64_t plane_bytes = 0;
   bool owns_planes = false;
   int32_t TR = 0;             // rows per walk (0: default)
-  int32_t nsweeps_step = 0;   // set by the caller before step()
-  int64_t rec_off = 0;        // offset of its records in the step buffer
+  int32_t nsweeps_step = 0;   // set by the caller before launch()
   potts_obs obs{};
   void *user = nullptr;       // owner's tag (serving loop)
+};
+
+// The records of one completed step: member mem[i] ran nsw[i] sweeps and
+// its records are base + off[i], [nsw[i]][1 + q].
+struct StepRecords {
+  const uint64_t *base = nullptr;
+  std::vector<Member *> mem;
+  std::vector<int32_t> nsw;
+  std::vector<int64_t> off;
 };
 
 class Engine {
  public:
   Engine() = default;
+  // Owners call release() while their stream is still alive; the
+  // destructor only frees what release() has not.
   ~Engine();
+  void release();
   Engine(const Engine &) = delete;
   Engine &operator=(const Engine &) = delete;
 
   int init(cudaStream_t stream);
   // Allocates and initialises a member's planes (ordered / random start)
-  // and its initial counts.  The engine does not take ownership of m.
+  // and, if initial_counts, its initial counts.  Stream-ordered: the first
+  // step after it sees the initialised planes.  The engine does not take
+  // ownership of m.
   int create_member(Member *m);
+  // Stream-ordered free: safe while steps that use the planes are queued.
   void free_member(Member *m);
   void set_members(const std::vector<Member *> &members);
   const std::vector<Member *> &members() const { return members_; }
 
-  // Runs max over members of nsweeps_step (<= k) sweeps; member m advances
-  // by m->nsweeps_step sweeps at inverse temperature m->beta.  Records of
-  // the step are in host memory afterwards: records(m) -> [nsweeps][1+q].
-  int step(int32_t k);
-  const uint64_t *records(const Member *m) const { return h_rec_ + m->rec_off; }
+  // Enqueues one step: member m runs m->nsweeps_step (<= k) sweeps at
+  // m->beta, from sweep index m->sweep_next.  Up to two steps are in flight;
+  // launching a third first completes the oldest.
+  int launch(int32_t k);
+  // Waits for the oldest launched step, applies its records to the members'
+  // observables and sweep counters, and makes them available as last().
+  int complete();
+  int in_flight() const { return (int)inflight_.size(); }
+  const StepRecords &last() const { return last_; }
+  int step(int32_t k);   // launch + complete
+  int drain();           // complete every launched step
 
   // Rows per walk and sweeps per graph chosen by timing candidates on a
   // scratch copy of the members' state (results do not depend on them).
@@ -91,7 +112,6 @@ class Engine {
   int32_t tuned_tr() const { return tuned_tr_; }
 
   int copy_spins(const Member *m, uint8_t *out_LxL);
-  size_t member_bytes(int32_t L) const;
 
   // Serving members skip the initial recount (their records come from the
   // sweeps), so admission does not wait for the device.
@@ -102,28 +122,42 @@ class Engine {
     LaunchParams *P = nullptr;
     bool lt0 = false;
     int32_t maxq = 2;
+    int lane = 0;             // stream lane (0: st_, 1: aux_)
   };
-  int ensure_capacity(int32_t k);
+  struct Slot {               // buffers of one in-flight step
+    StepDesc *d_step = nullptr, *h_step = nullptr;
+    size_t step_cap = 0;
+    unsigned long long *d_rec = nullptr;
+    uint64_t *h_rec = nullptr;
+    size_t rec_cap = 0, rec_used = 0;
+    cudaEvent_t done = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int32_t graph_k = -1;
+    uint64_t graph_gen = 0;
+    StepRecords rec;
+  };
+  int slot_capacity(Slot &sl, int32_t k);
   int rebuild();
-  int launch_all(int32_t kmax);
-  int capture(int32_t k);
-  void drop_graph();
+  int launch_all(Slot &sl, int32_t kmax);
+  int capture(Slot &sl, int32_t k);
   void drop_units();
 
   cudaStream_t st_ = nullptr;
+  cudaStream_t aux_ = nullptr;   // second lane, forked from st_ per step
+  cudaEvent_t fork_ = nullptr, join_ = nullptr;
+  int lanes_ = 1;
   cudaMemPool_t pool_ = nullptr;
   int sm_count_ = 1;
   std::vector<Member *> members_;
   std::vector<uint8_t> member_lt0_;
   bool dirty_ = true;
-  int32_t graph_k_ = -1;
-  cudaGraphExec_t gexec_ = nullptr;
+  uint64_t gen_ = 1;          // membership generation (graphs are per gen)
+  uint64_t stable_ = 0;       // launches since the last rebuild
   std::vector<Unit> units_;
-  StepDesc *d_step_ = nullptr, *h_step_ = nullptr;
-  size_t step_cap_ = 0;
-  unsigned long long *d_rec_ = nullptr;
-  uint64_t *h_rec_ = nullptr;
-  size_t rec_cap_ = 0, rec_used_ = 0;
+  Slot slots_[2];
+  int next_slot_ = 0;
+  std::vector<int> inflight_;
+  StepRecords last_;
   int32_t tuned_k_ = 16, tuned_tr_ = 0;
 };
 

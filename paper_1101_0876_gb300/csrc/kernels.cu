@@ -153,7 +153,8 @@ TileGeom choose_geom(int32_t L, int32_t H, int32_t q, int32_t sm_count,
       tr *= 2;
     }
   }
-  g.TR = std::min(tr, L);
+  // no longer than needed for the row groups of one tile to cover L
+  g.TR = std::max(1, std::min(tr, (L + g.RG - 1) / g.RG));
   g.ty = (L + g.RG * g.TR - 1) / (g.RG * g.TR);
   if ((int64_t)g.ty * g.gx >= 4 * max_ctas) {
     // plenty of tiles: one tile per CTA, the hardware balances the waves

@@ -9,6 +9,7 @@
 // lattices that are done, freeing their slot and memory.  Clients talk to
 // the loop only through the mutex-protected queue and outboxes
 // (potts_serve_submit / poll / cancel), which never block on the GPU.
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <chrono>
@@ -17,6 +18,7 @@
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 
 #include "engine.cuh"
 
@@ -31,10 +33,14 @@ struct Request {
   potts_req r{};
   ReqState state = ReqState::Queued;
   Member m;
-  int64_t remaining = 0;       // sweeps still to run
+  int64_t to_launch = 0;       // sweeps not yet launched
+  int64_t to_deliver = 0;      // sweeps whose records have not arrived
+  bool in_engine = false;      // holds planes and a slot
   std::vector<uint64_t> outbox;  // ready records, flattened
   size_t outbox_head = 0;      // first record not yet polled (in u64)
   bool cancel_requested = false;
+  bool forgotten = false;      // the client has seen the final state
+  uint64_t last_seq = 0;       // last launch that may reference it
   int error = POTTS_OK;
 };
 
@@ -48,11 +54,13 @@ struct potts_server {
   bool stop = false;
   std::deque<Request *> queue;
   std::unordered_map<uint64_t, Request *> all;
-  std::vector<Request *> active;
+  std::vector<Request *> active;   // admitted, in the engine
+  std::vector<Request *> retired;  // out of the engine, records in flight
   Engine eng;
   cudaStream_t st = nullptr;
   int device = 0;
   uint64_t next_id = 1;
+  uint64_t launch_seq = 0, complete_seq = 0;
   potts_serve_stats stats{};
   int loop_error = POTTS_OK;
   std::string loop_msg;
@@ -61,24 +69,66 @@ struct potts_server {
     return (uint64_t)r.L * (uint64_t)r.L;
   }
 
-  void retire(Request *q, ReqState s) {
+  // Leaves the engine: slot and memory are free for the next admission
+  // (the stream-ordered free runs after the steps already queued).
+  void leave_engine(Request *q) {
+    if (!q->in_engine) return;
     eng.free_member(&q->m);
     stats.bytes_in_use -= bytes_of(q->r);
-    q->state = s;
+    q->in_engine = false;
+    q->last_seq = launch_seq;
+  }
+
+  // Deletes retired requests that the client has finished with and that no
+  // in-flight step can still reference.
+  void reap() {
+    retired.erase(std::remove_if(retired.begin(), retired.end(),
+                                 [&](Request *q) {
+                                   if (q->forgotten &&
+                                       complete_seq >= q->last_seq) {
+                                     delete q;
+                                     return true;
+                                   }
+                                   return false;
+                                 }),
+                  retired.end());
+  }
+
+  void deliver() {
+    const StepRecords &r = eng.last();
+    std::lock_guard<std::mutex> lk(mu);
+    stats.steps += 1;
+    for (size_t i = 0; i < r.mem.size(); ++i) {
+      Request *q = static_cast<Request *>(r.mem[i]->user);
+      const int32_t n = r.nsw[i];
+      if (n <= 0) continue;
+      if (q->state == ReqState::Active) {
+        const uint64_t *rec = r.base + r.off[i];
+        q->outbox.insert(q->outbox.end(), rec, rec + (size_t)n * (1 + q->r.q));
+      }
+      q->to_deliver -= n;
+      stats.sweeps_done += (uint64_t)n;
+      stats.updates_done += (uint64_t)n * (uint64_t)q->r.L * (uint64_t)q->r.L;
+      if (q->to_deliver == 0 && q->state == ReqState::Active) {
+        q->state = ReqState::Done;
+        stats.completed += 1;
+      }
+    }
+    reap();
   }
 
   void run() {
     cudaSetDevice(device);
     std::vector<Member *> members;
+    bool changed = true;
     for (;;) {
       std::vector<Request *> admit;
       {
         std::unique_lock<std::mutex> lk(mu);
-        cv.wait_for(lk, std::chrono::milliseconds(50), [&] {
-          return stop || !queue.empty() || !active.empty();
-        });
+        if (active.empty() && eng.in_flight() == 0)
+          cv.wait_for(lk, std::chrono::milliseconds(50),
+                      [&] { return stop || !queue.empty(); });
         if (stop) break;
-        // cancellations of queued and active requests
         for (auto it = queue.begin(); it != queue.end();) {
           if ((*it)->cancel_requested) {
             (*it)->state = ReqState::Cancelled;
@@ -98,16 +148,31 @@ struct potts_server {
           stats.bytes_in_use += b;
           admit.push_back(q);
         }
+        // cancellations of admitted requests
+        for (size_t i = 0; i < active.size();) {
+          Request *q = active[i];
+          if (q->cancel_requested) {
+            q->state = ReqState::Cancelled;
+            stats.cancelled += 1;
+            leave_engine(q);
+            retired.push_back(q);
+            active.erase(active.begin() + (int64_t)i);
+            changed = true;
+          } else {
+            ++i;
+          }
+        }
       }
-      // allocate + initialise outside the lock
-      for (Request *q : admit) {
+      for (Request *q : admit) {  // allocation + init are stream-ordered
         q->m.L = q->r.L;
         q->m.q = q->r.q;
         q->m.start = q->r.start;
         q->m.seed = q->r.seed;
         q->m.beta = q->r.beta;
-        q->remaining = q->r.nsweeps;
-        int rc = eng.create_member(&q->m);
+        q->m.user = q;
+        q->to_launch = q->r.nsweeps;
+        q->to_deliver = q->r.nsweeps;
+        const int rc = eng.create_member(&q->m);
         std::lock_guard<std::mutex> lk(mu);
         if (rc != POTTS_OK) {
           q->error = rc;
@@ -115,66 +180,86 @@ struct potts_server {
           q->state = ReqState::Failed;
           continue;
         }
+        q->in_engine = true;
         q->state = ReqState::Active;
         stats.admitted += 1;
         active.push_back(q);
+        changed = true;
       }
-      bool changed = !admit.empty();
+      const int32_t k = std::max(1, cfg.sweeps_per_step);
+      bool launched = false;
+      if (!active.empty()) {
+        if (changed) {
+          members.clear();
+          for (Request *q : active) members.push_back(&q->m);
+          eng.set_members(members);
+          changed = false;
+        }
+        for (Request *q : active) {
+          q->m.nsweeps_step = (int32_t)std::min<int64_t>(q->to_launch, k);
+          q->to_launch -= q->m.nsweeps_step;
+        }
+        int rc = eng.launch(k);
+        if (rc == POTTS_OK) {
+          launched = true;
+          std::lock_guard<std::mutex> lk(mu);
+          launch_seq += 1;
+          for (size_t i = 0; i < active.size();) {
+            Request *q = active[i];
+            if (q->to_launch == 0) {  // all its sweeps are queued
+              leave_engine(q);
+              retired.push_back(q);
+              active.erase(active.begin() + (int64_t)i);
+              changed = true;
+            } else {
+              ++i;
+            }
+          }
+        } else {
+          fail_all(rc);
+          members.clear();
+          eng.set_members(members);
+          continue;
+        }
+      }
+      if (eng.in_flight() == 2 || (!launched && eng.in_flight() > 0)) {
+        const int rc = eng.complete();
+        if (rc != POTTS_OK) {
+          fail_all(rc);
+          continue;
+        }
+        complete_seq += 1;
+        deliver();
+        cv.notify_all();
+      }
       {
         std::lock_guard<std::mutex> lk(mu);
-        for (size_t i = 0; i < active.size();) {
-          Request *q = active[i];
-          if (q->cancel_requested || q->remaining == 0) {
-            if (q->cancel_requested) stats.cancelled += 1;
-            else stats.completed += 1;
-            retire(q, q->cancel_requested ? ReqState::Cancelled
-                                          : ReqState::Done);
-            active.erase(active.begin() + (int64_t)i);
-            changed = true;
-          } else {
-            ++i;
-          }
-        }
         stats.active = (int32_t)active.size();
         stats.queued = (int32_t)queue.size();
       }
-      if (active.empty()) continue;
-      const int32_t k = std::max(1, cfg.sweeps_per_step);
-      if (changed) {
-        members.clear();
-        for (Request *q : active) members.push_back(&q->m);
-        eng.set_members(members);
-      }
-      for (Request *q : active)
-        q->m.nsweeps_step = (int32_t)std::min<int64_t>(q->remaining, k);
-      const int rc = eng.step(k);
-      std::lock_guard<std::mutex> lk(mu);
-      if (rc != POTTS_OK) {
-        loop_error = rc;
-        loop_msg = potts_last_error();
-        for (Request *q : active) {
-          q->error = rc;
-          retire(q, ReqState::Failed);
-        }
-        active.clear();
-        members.clear();
-        eng.set_members(members);
-        continue;
-      }
-      stats.steps += 1;
-      for (Request *q : active) {
-        const int32_t n = q->m.nsweeps_step;
-        const uint64_t *rec = eng.records(&q->m);
-        q->outbox.insert(q->outbox.end(), rec, rec + (size_t)n * (1 + q->r.q));
-        q->remaining -= n;
-        stats.sweeps_done += (uint64_t)n;
-        stats.updates_done += (uint64_t)n * (uint64_t)q->r.L * (uint64_t)q->r.L;
-      }
-      cv.notify_all();
     }
-    // shutdown: free everything still held
+    // shutdown: finish what is in flight, free everything still held
+    eng.drain();
     std::lock_guard<std::mutex> lk(mu);
-    for (Request *q : active) retire(q, ReqState::Cancelled);
+    for (Request *q : active) {
+      leave_engine(q);
+      q->state = ReqState::Cancelled;
+    }
+    active.clear();
+  }
+
+  void fail_all(int rc) {
+    eng.drain();
+    std::lock_guard<std::mutex> lk(mu);
+    complete_seq = launch_seq;
+    loop_error = rc;
+    loop_msg = potts_last_error();
+    for (Request *q : active) {
+      q->error = rc;
+      q->state = ReqState::Failed;
+      leave_engine(q);
+      retired.push_back(q);
+    }
     active.clear();
   }
 };
@@ -201,6 +286,7 @@ int potts_serve_start(const potts_serve_cfg *cfg, potts_server_h *out) {
   }
   int rc = s->eng.init(s->st);
   if (rc != POTTS_OK) {
+    s->eng.release();
     cudaStreamDestroy(s->st);
     delete s;
     return rc;
@@ -209,6 +295,7 @@ int potts_serve_start(const potts_serve_cfg *cfg, potts_server_h *out) {
   try {
     s->th = std::thread([s] { s->run(); });
   } catch (...) {
+    s->eng.release();
     cudaStreamDestroy(s->st);
     delete s;
     return fail(POTTS_ENOMEM, "could not start the server thread");
@@ -290,7 +377,14 @@ int potts_serve_poll(potts_server_h s, uint64_t req_id, uint64_t *out_counts,
   }
   if (*done) {
     s->all.erase(it);
-    delete q;
+    // a request that went through the engine stays on the retired list
+    // until no in-flight step can reference it; the loop deletes it then
+    const bool held = std::find(s->retired.begin(), s->retired.end(), q) !=
+                          s->retired.end() ||
+                      std::find(s->active.begin(), s->active.end(), q) !=
+                          s->active.end();
+    if (held) q->forgotten = true;
+    else delete q;
   }
   return rc;
 }
@@ -324,12 +418,16 @@ int potts_serve_stop(potts_server_h s) {
   }
   s->cv.notify_all();
   if (s->th.joinable()) s->th.join();
-  for (auto &kv : s->all) delete kv.second;
-  s->all.clear();
-  if (s->st) {
-    cudaStreamSynchronize(s->st);
-    cudaStreamDestroy(s->st);
+  {
+    std::unordered_set<Request *> owned;
+    for (auto &kv : s->all) owned.insert(kv.second);
+    for (Request *q : s->retired) owned.insert(q);
+    for (Request *q : owned) delete q;
+    s->all.clear();
+    s->retired.clear();
   }
+  s->eng.release();  // uses the stream: before it is destroyed
+  if (s->st) cudaStreamDestroy(s->st);
   int rc = s->loop_error;
   delete s;
   return rc == POTTS_OK ? POTTS_OK : fail(rc, "server loop had failed");

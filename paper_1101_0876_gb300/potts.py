@@ -348,9 +348,10 @@ class Server:
                 return None
             raise
 
-    def poll(self, rid: int, max_sweeps: int = 4096):
+    def poll(self, rid: int, max_sweeps: int = 4096, out=None):
         """Returns (records array (n, 1+q), done).  Raises PottsError for a
-        cancelled, failed or unknown request."""
+        cancelled, failed or unknown request.  `out` (uint64, C-contiguous,
+        at least max_sweeps * (1+q) values) is reused if given."""
         q = self._q.get(rid)
         n = ctypes.c_int64()
         done = ctypes.c_int()
@@ -359,7 +360,13 @@ class Server:
                                          ctypes.POINTER(ctypes.c_uint64)(), 0,
                                          ctypes.byref(n), ctypes.byref(done)))
             return np.empty((0, 0), dtype=np.uint64), bool(done.value)
-        out = np.empty((int(max_sweeps), 1 + q), dtype=np.uint64)
+        if out is None:
+            out = np.empty((int(max_sweeps), 1 + q), dtype=np.uint64)
+        else:
+            assert out.dtype == np.uint64 and out.flags.c_contiguous
+            assert out.size >= int(max_sweeps) * (1 + q)
+            out = out.reshape(-1)[:int(max_sweeps) * (1 + q)].reshape(
+                int(max_sweeps), 1 + q)
         rc = lib().potts_serve_poll(self._h, int(rid),
                                     _ptr(out, ctypes.c_uint64),
                                     int(max_sweeps), ctypes.byref(n),
