@@ -331,6 +331,9 @@ def run_ours(args):
                      "bytes_per_launch": bytes_per_launch},
         "clocks": clocks.summary(),
     }
+    if ws == 1 and not args.no_u4:
+        lat.close()
+        line["u4"] = measure_u4(args, L, q, betas)
     if ws == 1 and not args.no_batched:
         lat.close()
         line["batched"] = measure_batched(args, line["updates_per_s"])
@@ -346,6 +349,35 @@ def run_ours(args):
                       f"{sweeps} sweeps ({dt:.1f} s); per-update cost of the "
                       f"serial raster loop does not depend on L"}
     return line
+
+
+# ------------------------------------------------- packed 4-bit layout
+def measure_u4(args, L, q, betas):
+    """The same workload in the packed 4-bit layout (q <= 16): 1.5 bytes
+    per site per sweep, device-timed like `value`."""
+    import torch
+    from paper_1101_0876_gb300 import potts
+    stream = torch.cuda.Stream()
+    lat = potts.Lattice(L, q, potts.START_RANDOM, 11, layout=potts.LAYOUT_U4)
+    lat.set_stream(stream.cuda_stream)
+    lat.sweep(betas[0], 3, records=False)
+    n = max(3, args.steps // 2)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.sweep(betas[1], n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    lat.close()
+    N = L * L
+    hbm, _ = measured_peaks()
+    gbs = 1.5 * N * n / (ms * 1e-3) / 1e9
+    return {"value": ms * 1e6 / (N * n), "unit": UNIT, "sweeps": n,
+            "updates_per_s": N * n / (ms * 1e-3),
+            "bytes_per_update": 1.5, "achieved_gbs": gbs,
+            "frac_hbm": gbs / hbm}
 
 
 # ------------------------------------------------- batched / served
@@ -489,6 +521,7 @@ def main():
     ap.add_argument("--cpu-L", type=int, default=2048)
     ap.add_argument("--cpu-sweeps", type=int, default=40)
     ap.add_argument("--ref-L", type=int, default=1024)
+    ap.add_argument("--no-u4", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--batch-sweeps", type=int, default=500)

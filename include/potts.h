@@ -70,7 +70,8 @@ enum { POTTS_START_ORDERED = 0, POTTS_START_RANDOM = 1 };
 /* Spin storage in device memory.  U8: one byte per spin, two colour planes
  * of L rows x L/2 bytes (the paper's byte-per-spin colour-packed layout,
  * Sec. 3.3).  U4: two spins per byte (q <= 16), planes of L rows x L/4
- * bytes.  AUTO picks U8. */
+ * bytes, site 2b of a plane row in the low nibble of byte b and site 2b+1
+ * in the high nibble; half the memory traffic.  AUTO picks U8. */
 enum { POTTS_LAYOUT_AUTO = 0, POTTS_LAYOUT_U8 = 1, POTTS_LAYOUT_U4 = 2 };
 
 typedef struct potts_lattice *potts_h;
@@ -89,8 +90,9 @@ int potts_version(void);
  * device and initialises it: ORDERED = every spin 0 (the paper's s_i = 1,
  * Sec. 3 protocol); RANDOM = i.i.d. uniform spins drawn from the Philox
  * words of domain 2 + colour at sweep 0 (s = floor(u q / 2^32)).
- * Constraints: 32 <= L <= 65536, L % 32 == 0 (U4 needs L % 64 == 0);
- * 2 <= q <= 256 (U4 needs q <= 16).  The sweep index starts at 0.
+ * Constraints: 32 <= L <= 65536, L % 32 == 0; 2 <= q <= 256 (U4 needs
+ * q <= 16).  Both layouts give identical results.  The sweep index starts
+ * at 0.
  * Errors: EINVAL, ENOMEM, ECUDA. */
 int potts_create(int32_t L, int32_t q, int32_t start, uint64_t seed,
                  potts_h *out);

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_BATCH_MINB)
                       const StepDesc *__restrict__ S, int32_t s) {
   constexpr bool COUNTS = COLOUR == 1;
   extern __shared__ uint32_t s_hist[];
-  __shared__ __align__(16) uint32_t s_tab[9 * 4];
+  __shared__ __align__(16) uint32_t s_tab[kTabWords];
   __shared__ uint32_t s_sat;
   const uint32_t tid = threadIdx.x;
   const int32_t bid = (int32_t)blockIdx.x;
@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_BATCH_MINB)
   const StepDesc &sd = S[d.step];
   if (s >= sd.nsweeps) return;  // same for the whole CTA
   const uint32_t q = (uint32_t)d.q;
-  if (tid < 9) s_tab[tid * 4] = sd.tab[tid];
+  for (uint32_t i = tid; i < (uint32_t)kTabWords; i += kPassThreads)
+    s_tab[i] = (i % 4u == 0 && i / 4u < 9u) ? sd.tab[i / 4u] : 0u;
   for (uint32_t v = tid; v < q * 32u; v += kPassThreads) s_hist[v] = 0;
   if (tid == 0) s_sat = 0;
   __syncthreads();
@@ -57,6 +58,8 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_BATCH_MINB)
   A.t_hi = (uint32_t)(t0 >> 32);
   A.key0 = d.key0;
   A.key1 = d.key1;
+  A.hist_bins = q;
+  A.layout = kLayoutU8;
   const PhiloxKey ks = philox_schedule(A.key0, A.key1);
   const int32_t lt = bid - d.tile0;
   const int32_t tx = lt % d.gx, ty = lt / d.gx;
@@ -191,9 +194,9 @@ int Engine::create_member(Member *m) {
     POTTS_CK(cudaMemsetAsync(m->planes, 0, (size_t)(2 * m->plane_bytes), st_));
   } else {
     POTTS_CK(launch_init_random(m->planes, m->plane_bytes, (uint32_t)m->q, 0,
-                                m->seed, st_));
+                                m->seed, kLayoutU8, st_));
     POTTS_CK(launch_init_random(m->planes + m->plane_bytes, m->plane_bytes,
-                                (uint32_t)m->q, 1, m->seed, st_));
+                                (uint32_t)m->q, 1, m->seed, kLayoutU8, st_));
   }
   if (!initial_counts) return POTTS_OK;
   unsigned long long *d = nullptr;
@@ -201,7 +204,7 @@ int Engine::create_member(Member *m) {
                                    (size_t)(1 + m->q) * 8, pool_, st_));
   POTTS_CK(cudaMemsetAsync(d, 0, (size_t)(1 + m->q) * 8, st_));
   POTTS_CK(launch_recount(m->planes, m->planes + m->plane_bytes, m->L,
-                          m->L / 2, (uint32_t)m->q, d, st_));
+                          m->L / 2, (uint32_t)m->q, kLayoutU8, d, st_));
   std::vector<uint64_t> h((size_t)(1 + m->q));
   POTTS_CK(cudaMemcpyAsync(h.data(), d, h.size() * 8, cudaMemcpyDeviceToHost,
                            st_));

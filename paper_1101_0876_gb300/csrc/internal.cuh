@@ -60,14 +60,14 @@ AcceptTable accept_table(const uint64_t thr[5]);
 cudaError_t launch_pass(const PassArgs &A, const AcceptTable &T,
                         const TileGeom &G, unsigned long long *rec,
                         cudaStream_t st);
-// Random start of one plane: s = floor(u q / 2^32), u = Philox word of
-// domain 2 + colour at sweep 0.
-cudaError_t launch_init_random(uint8_t *plane, int64_t plane_bytes, uint32_t q,
-                               uint32_t colour, uint64_t seed,
-                               cudaStream_t st);
+// Random start of one plane of plane_sites sites: s = floor(u q / 2^32),
+// u = Philox word of domain 2 + colour at sweep 0.
+cudaError_t launch_init_random(uint8_t *plane, int64_t plane_sites,
+                               uint32_t q, uint32_t colour, uint64_t seed,
+                               uint32_t layout, cudaStream_t st);
 // Recount {B, hist} from the planes into rec (must start at zero).
 cudaError_t launch_recount(const uint8_t *white, const uint8_t *black,
-                           int32_t L, int32_t H, uint32_t q,
+                           int32_t L, int32_t H, uint32_t q, uint32_t layout,
                            unsigned long long *rec, cudaStream_t st);
 
 int sm_count_of_current_device();

@@ -18,19 +18,20 @@ namespace potts {
 // non-empty bin per CTA, without a second kernel or a CPU-side sum).
 constexpr int kPairBins = 256;
 
-template <int QB, int COLOUR, bool PAIRS, bool LT0>
+template <int QB, int COLOUR, bool PAIRS, bool LT0, int LAY>
 __global__ void __launch_bounds__(kPassThreads, POTTS_PASS_MINB)
     pass_kernel(PassArgs A, AcceptTable Tin, TileGeom G,
                 unsigned long long *rec) {
   constexpr bool COUNTS = COLOUR == 1;
   extern __shared__ uint32_t s_hist[];  // bins * 32 (bins = 256 or q)
-  __shared__ __align__(16) uint32_t s_tab[9 * 4];
+  __shared__ __align__(16) uint32_t s_tab[kTabWords];
   __shared__ uint32_t s_sat;
   __shared__ uint32_t s_fold[16];
   const uint32_t tid = threadIdx.x;
-  const uint32_t bins = PAIRS ? (uint32_t)kPairBins : A.q;
+  const uint32_t bins = PAIRS ? (uint32_t)kPairBins : A.hist_bins;
   const bool hist = rec != nullptr;
-  if (tid < 9) s_tab[tid * 4] = Tin.tab[tid];
+  for (uint32_t i = tid; i < (uint32_t)kTabWords; i += kPassThreads)
+    s_tab[i] = (i % 4u == 0 && i / 4u < 9u) ? Tin.tab[i / 4u] : 0u;
   if (hist) {
     for (uint32_t v = tid; v < bins * 32u; v += kPassThreads) s_hist[v] = 0;
     if (tid < 16) s_fold[tid] = 0;
@@ -47,7 +48,7 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_PASS_MINB)
       const int32_t i0 = (tile * G.RG + rg) * G.TR;
       if (i0 >= A.L) continue;
       const int32_t rows = min(G.TR, A.L - i0);
-      walk_column<QB, COLOUR, COUNTS, PAIRS, LT0>(
+      walk_column<QB, COLOUR, COUNTS, PAIRS, LT0, LAY>(
           A, ks, reinterpret_cast<const uint8_t *>(s_tab), chunk * 16, i0,
           rows, hist ? s_hist + (tid & 31u) : nullptr, &ne);
       rows_done += (uint32_t)rows;
@@ -86,17 +87,20 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_PASS_MINB)
   }
 }
 
-template <int QB, int COLOUR, bool PAIRS>
+template <int QB, int COLOUR, bool PAIRS, int LAY = kLayoutU8>
 static cudaError_t launch_c(const PassArgs &A, const AcceptTable &T,
                             const TileGeom &G, unsigned long long *rec,
                             cudaStream_t st) {
   dim3 grid(G.gx, G.gy), block(kPassThreads);
   const size_t smem =
-      rec ? (size_t)(PAIRS ? kPairBins : A.q) * 32u * sizeof(uint32_t) : 0;
+      rec ? (size_t)(PAIRS ? kPairBins : A.hist_bins) * 32u * sizeof(uint32_t)
+          : 0;
   if (T.rule_lt0)
-    pass_kernel<QB, COLOUR, PAIRS, true><<<grid, block, smem, st>>>(A, T, G, rec);
+    pass_kernel<QB, COLOUR, PAIRS, true, LAY>
+        <<<grid, block, smem, st>>>(A, T, G, rec);
   else
-    pass_kernel<QB, COLOUR, PAIRS, false><<<grid, block, smem, st>>>(A, T, G, rec);
+    pass_kernel<QB, COLOUR, PAIRS, false, LAY>
+        <<<grid, block, smem, st>>>(A, T, G, rec);
   return cudaGetLastError();
 }
 
@@ -105,6 +109,13 @@ static cudaError_t launch_qb(const PassArgs &A, const AcceptTable &T,
                              const TileGeom &G, unsigned long long *rec,
                              cudaStream_t st) {
   if constexpr (QB == 4) {
+    if (A.layout == kLayoutU4) {
+      if (G.pairs)
+        return A.colour ? launch_c<QB, 1, true, kLayoutU4>(A, T, G, rec, st)
+                        : launch_c<QB, 0, true, kLayoutU4>(A, T, G, rec, st);
+      return A.colour ? launch_c<QB, 1, false, kLayoutU4>(A, T, G, rec, st)
+                      : launch_c<QB, 0, false, kLayoutU4>(A, T, G, rec, st);
+    }
     if (G.pairs)
       return A.colour ? launch_c<QB, 1, true>(A, T, G, rec, st)
                       : launch_c<QB, 0, true>(A, T, G, rec, st);
@@ -116,6 +127,7 @@ static cudaError_t launch_qb(const PassArgs &A, const AcceptTable &T,
 cudaError_t launch_pass(const PassArgs &A, const AcceptTable &T,
                         const TileGeom &G, unsigned long long *rec,
                         cudaStream_t st) {
+  if (A.layout == kLayoutU4 && A.q > 16) return cudaErrorInvalidValue;
   switch (qbits_for((int32_t)A.q)) {
     case 4: return launch_qb<4>(A, T, G, rec, st);
     case 5: return launch_qb<5>(A, T, G, rec, st);
@@ -178,9 +190,11 @@ TileGeom choose_geom(int32_t L, int32_t H, int32_t q, int32_t sm_count,
 }
 
 // -------------------------------------------------------- random start
+// One thread per 16 sites of a plane (site index = byte index for U8):
+// s = floor(u q / 2^32), u = Philox word of domain 2 + colour at sweep 0.
 __global__ void init_random_kernel(uint8_t *plane, int64_t nchunks,
                                    uint32_t q, uint32_t domain, uint32_t key0,
-                                   uint32_t key1) {
+                                   uint32_t key1, uint32_t layout) {
   const PhiloxKey ks = philox_schedule(key0, key1);
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks;
        c += (int64_t)gridDim.x * blockDim.x) {
@@ -194,19 +208,24 @@ __global__ void init_random_kernel(uint8_t *plane, int64_t nchunks,
       const uint32_t p3 = (uint32_t)(((uint64_t)u.w * q) >> 32);
       w[j] = pack4(p0, p1, p2, p3);
     }
-    reinterpret_cast<uint4 *>(plane)[c] = make_uint4(w[0], w[1], w[2], w[3]);
+    if (layout == kLayoutU4)
+      reinterpret_cast<uint2 *>(plane)[c] =
+          make_uint2(pack8(w[0], w[1]), pack8(w[2], w[3]));
+    else
+      reinterpret_cast<uint4 *>(plane)[c] = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
-cudaError_t launch_init_random(uint8_t *plane, int64_t plane_bytes, uint32_t q,
-                               uint32_t colour, uint64_t seed,
-                               cudaStream_t st) {
-  const int64_t nchunks = plane_bytes / 16;
+cudaError_t launch_init_random(uint8_t *plane, int64_t plane_sites,
+                               uint32_t q, uint32_t colour, uint64_t seed,
+                               uint32_t layout, cudaStream_t st) {
+  const int64_t nchunks = plane_sites / 16;
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((nchunks + threads - 1) / threads,
                                            (int64_t)1 << 20);
   init_random_kernel<<<(unsigned)blocks, threads, 0, st>>>(
-      plane, nchunks, q, 2u + colour, (uint32_t)seed, (uint32_t)(seed >> 32));
+      plane, nchunks, q, 2u + colour, (uint32_t)seed, (uint32_t)(seed >> 32),
+      layout);
   return cudaGetLastError();
 }
 
@@ -214,9 +233,11 @@ cudaError_t launch_init_random(uint8_t *plane, int64_t plane_bytes, uint32_t q,
 // One thread per 16-byte chunk of a black row: satisfied bonds of the 16
 // black sites with their four white neighbours, and the states of those
 // black sites and of the white sites at the same (i, x).
+template <int LAY>
 __global__ void recount_kernel(const uint8_t *white, const uint8_t *black,
                                int32_t L, int32_t H, uint32_t q,
                                unsigned long long *rec) {
+  using IO = Lay<LAY>;
   extern __shared__ uint32_t s_hist[];
   __shared__ uint32_t s_sat;
   const uint32_t tid = threadIdx.x;
@@ -225,22 +246,24 @@ __global__ void recount_kernel(const uint8_t *white, const uint8_t *black,
   __syncthreads();
   const int64_t nch = (int64_t)L * (H / 16);
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + tid;
+  const int32_t RB = IO::row_bytes(H);
   uint32_t sat = 0;
   if (c < nch) {
     const int32_t i = (int32_t)(c / (H / 16));
     const int32_t x0 = (int32_t)(c % (H / 16)) * 16;
+    const int32_t xb = LAY == kLayoutU4 ? x0 / 2 : x0;
     const int32_t im = i == 0 ? L - 1 : i - 1, ip = i + 1 == L ? 0 : i + 1;
-    const uint4 U = *reinterpret_cast<const uint4 *>(white + (int64_t)im * H + x0);
-    const uint4 D = *reinterpret_cast<const uint4 *>(white + (int64_t)ip * H + x0);
-    const uint4 C = *reinterpret_cast<const uint4 *>(white + (int64_t)i * H + x0);
-    const uint4 S = *reinterpret_cast<const uint4 *>(black + (int64_t)i * H + x0);
+    uint32_t Uw[4], Dw[4], Cw[4], Sw[4];
+    IO::load(white + (int64_t)im * RB + xb, false, Uw);
+    IO::load(white + (int64_t)ip * RB + xb, false, Dw);
+    IO::load(white + (int64_t)i * RB + xb, false, Cw);
+    IO::load(black + (int64_t)i * RB + xb, false, Sw);
     const bool left = ((i + 1) & 1) == 0;  // black: x-1 when i+1 even
-    const int32_t xe = left ? (x0 == 0 ? H - 4 : x0 - 4) : (x0 + 16 == H ? 0 : x0 + 16);
-    const uint32_t ew = *reinterpret_cast<const uint32_t *>(white + (int64_t)i * H + xe);
-    const uint32_t Cw[4] = {C.x, C.y, C.z, C.w};
-    const uint32_t Uw[4] = {U.x, U.y, U.z, U.w};
-    const uint32_t Dw[4] = {D.x, D.y, D.z, D.w};
-    const uint32_t Sw[4] = {S.x, S.y, S.z, S.w};
+    const int32_t xe = left ? (x0 == 0 ? RB - 4 : xb - 4)
+                            : (x0 + 16 == H ? 0 : xb + IO::kChunkBytes);
+    const uint32_t ew = IO::edge(
+        *reinterpret_cast<const uint32_t *>(white + (int64_t)i * RB + xe),
+        left);
     uint32_t Wd[4];
     if (left) {
       Wd[0] = __funnelshift_l(ew, Cw[0], 8);
@@ -271,13 +294,18 @@ __global__ void recount_kernel(const uint8_t *white, const uint8_t *black,
 }
 
 cudaError_t launch_recount(const uint8_t *white, const uint8_t *black,
-                           int32_t L, int32_t H, uint32_t q,
+                           int32_t L, int32_t H, uint32_t q, uint32_t layout,
                            unsigned long long *rec, cudaStream_t st) {
   const int64_t nch = (int64_t)L * (H / 16);
   const int threads = 256;
   const int64_t blocks = (nch + threads - 1) / threads;
-  recount_kernel<<<(unsigned)blocks, threads, (size_t)q * 32u * 4u, st>>>(
-      white, black, L, H, q, rec);
+  const size_t smem = (size_t)q * 32u * 4u;
+  if (layout == kLayoutU4)
+    recount_kernel<kLayoutU4><<<(unsigned)blocks, threads, smem, st>>>(
+        white, black, L, H, q, rec);
+  else
+    recount_kernel<kLayoutU8><<<(unsigned)blocks, threads, smem, st>>>(
+        white, black, L, H, q, rec);
   return cudaGetLastError();
 }
 

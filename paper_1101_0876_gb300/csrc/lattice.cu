@@ -116,6 +116,19 @@ void rowmajor_to_planes(const uint8_t *in, int32_t L, uint8_t *white,
   }
 }
 
+// U4 plane (L rows x L/4 bytes, site 2b in the low nibble of byte b) <->
+// U8 plane (L rows x L/2 bytes).
+static void u4_to_u8(const uint8_t *in, int64_t nbytes, uint8_t *out) {
+  for (int64_t b = 0; b < nbytes; ++b) {
+    out[2 * b] = in[b] & 0x0F;
+    out[2 * b + 1] = in[b] >> 4;
+  }
+}
+static void u8_to_u4(const uint8_t *in, int64_t nbytes, uint8_t *out) {
+  for (int64_t b = 0; b < nbytes; ++b)
+    out[b] = (uint8_t)((in[2 * b] & 0x0F) | (in[2 * b + 1] << 4));
+}
+
 }  // namespace potts
 
 using namespace potts;
@@ -143,7 +156,8 @@ static int recount_into_obs(potts_h h) {
   const int32_t q = h->q;
   POTTS_CK(cudaMemsetAsync(h->d_rec, 0, (size_t)(1 + q) * 8, h->stream));
   POTTS_CK(launch_recount(h->d_planes, h->d_planes + h->plane_bytes, h->L,
-                          h->H, (uint32_t)q, h->d_rec, h->stream));
+                          h->H, (uint32_t)q, (uint32_t)h->layout, h->d_rec,
+                          h->stream));
   POTTS_CK(cudaMemcpyAsync(h->h_rec, h->d_rec, (size_t)(1 + q) * 8,
                            cudaMemcpyDeviceToHost, h->stream));
   POTTS_CK(cudaStreamSynchronize(h->stream));
@@ -178,8 +192,10 @@ int potts_create_ex(int32_t L, int32_t q, int32_t start, uint64_t seed,
   if (!out) return fail(POTTS_EINVAL, "out is NULL");
   *out = nullptr;
   if (layout == POTTS_LAYOUT_AUTO) layout = POTTS_LAYOUT_U8;
-  if (layout != POTTS_LAYOUT_U8)
-    return fail(POTTS_EINVAL, "layout %d is not available", layout);
+  if (layout != POTTS_LAYOUT_U8 && layout != POTTS_LAYOUT_U4)
+    return fail(POTTS_EINVAL, "layout must be 0 (auto), 1 (U8) or 2 (U4)");
+  if (layout == POTTS_LAYOUT_U4 && q > 16)
+    return fail(POTTS_EINVAL, "the packed 4-bit layout needs q <= 16 (got %d)", q);
   if (L < 32 || L > 65536 || L % 32 != 0)
     return fail(POTTS_EINVAL, "L must be a multiple of 32 in [32, 65536] (got %d)", L);
   if (q < 2 || q > 256) return fail(POTTS_EINVAL, "q must be in [2, 256] (got %d)", q);
@@ -192,7 +208,7 @@ int potts_create_ex(int32_t L, int32_t q, int32_t start, uint64_t seed,
   h->H = L / 2;
   h->layout = layout;
   h->seed = seed;
-  h->plane_bytes = (int64_t)L * (L / 2);
+  h->plane_bytes = (int64_t)L * (layout == POTTS_LAYOUT_U4 ? L / 4 : L / 2);
   int rc = POTTS_OK;
   do {
     cudaError_t e = cudaGetDevice(&h->device);
@@ -218,9 +234,13 @@ int potts_create_ex(int32_t L, int32_t q, int32_t start, uint64_t seed,
     if (start == POTTS_START_ORDERED) {
       e = cudaMemsetAsync(h->d_planes, 0, (size_t)(2 * h->plane_bytes), h->stream);
     } else {
-      e = launch_init_random(h->d_planes, h->plane_bytes, (uint32_t)q, 0, seed, h->stream);
+      const int64_t sites = (int64_t)L * (L / 2);
+      e = launch_init_random(h->d_planes, sites, (uint32_t)q, 0, seed,
+                             (uint32_t)layout, h->stream);
       if (e == cudaSuccess)
-        e = launch_init_random(h->d_planes + h->plane_bytes, h->plane_bytes, (uint32_t)q, 1, seed, h->stream);
+        e = launch_init_random(h->d_planes + h->plane_bytes, sites,
+                               (uint32_t)q, 1, seed, (uint32_t)layout,
+                               h->stream);
     }
     if (e != cudaSuccess) { rc = fail(POTTS_ECUDA, "init: %s", cudaGetErrorString(e)); break; }
     rc = recount_into_obs(h);
@@ -258,6 +278,8 @@ int potts_sweep(potts_h h, double beta, int64_t nsweeps, uint64_t *out_counts) {
     A[c].colour = (uint32_t)c;
     A[c].key0 = (uint32_t)h->seed;
     A[c].key1 = (uint32_t)(h->seed >> 32);
+    A[c].hist_bins = (uint32_t)q;
+    A[c].layout = (uint32_t)h->layout;
   }
   int64_t done = 0;
   while (done < nsweeps) {
@@ -313,7 +335,20 @@ int potts_get_spins(potts_h h, uint8_t *out_LxL) {
   POTTS_CK(cudaMemcpyAsync(tmp.data(), h->d_planes, tmp.size(),
                            cudaMemcpyDeviceToHost, h->stream));
   POTTS_CK(cudaStreamSynchronize(h->stream));
-  planes_to_rowmajor(tmp.data(), tmp.data() + h->plane_bytes, h->L, out_LxL);
+  if (h->layout == POTTS_LAYOUT_U4) {
+    std::vector<uint8_t> u8;
+    const int64_t sites = (int64_t)h->L * h->H;
+    try {
+      u8.resize((size_t)(2 * sites));
+    } catch (...) {
+      return fail(POTTS_ENOMEM, "host allocation failed");
+    }
+    u4_to_u8(tmp.data(), h->plane_bytes, u8.data());
+    u4_to_u8(tmp.data() + h->plane_bytes, h->plane_bytes, u8.data() + sites);
+    planes_to_rowmajor(u8.data(), u8.data() + sites, h->L, out_LxL);
+  } else {
+    planes_to_rowmajor(tmp.data(), tmp.data() + h->plane_bytes, h->L, out_LxL);
+  }
   return POTTS_OK;
 }
 
@@ -330,7 +365,20 @@ int potts_set_state(potts_h h, const uint8_t *LxL, uint64_t sweep) {
   } catch (...) {
     return fail(POTTS_ENOMEM, "host allocation failed");
   }
-  rowmajor_to_planes(LxL, h->L, tmp.data(), tmp.data() + h->plane_bytes);
+  if (h->layout == POTTS_LAYOUT_U4) {
+    std::vector<uint8_t> u8;
+    const int64_t sites = (int64_t)h->L * h->H;
+    try {
+      u8.resize((size_t)(2 * sites));
+    } catch (...) {
+      return fail(POTTS_ENOMEM, "host allocation failed");
+    }
+    rowmajor_to_planes(LxL, h->L, u8.data(), u8.data() + sites);
+    u8_to_u4(u8.data(), h->plane_bytes, tmp.data());
+    u8_to_u4(u8.data() + sites, h->plane_bytes, tmp.data() + h->plane_bytes);
+  } else {
+    rowmajor_to_planes(LxL, h->L, tmp.data(), tmp.data() + h->plane_bytes);
+  }
   POTTS_CK(cudaMemcpyAsync(h->d_planes, tmp.data(), tmp.size(),
                            cudaMemcpyHostToDevice, h->stream));
   POTTS_CK(cudaStreamSynchronize(h->stream));
@@ -352,7 +400,8 @@ int potts_device_planes(potts_h h, void **white, void **black,
   if (!h) return fail(POTTS_EINVAL, "handle is NULL");
   if (white) *white = h->d_planes;
   if (black) *black = h->d_planes + h->plane_bytes;
-  if (row_bytes) *row_bytes = h->H;
+  if (row_bytes)
+    *row_bytes = h->layout == POTTS_LAYOUT_U4 ? h->H / 2 : h->H;
   if (layout) *layout = h->layout;
   return POTTS_OK;
 }

@@ -91,6 +91,10 @@ extern "C" int potts_sweep_planes_noalloc(void *white, void *black, int32_t L,
     A[c].colour = (uint32_t)c;
     A[c].key0 = (uint32_t)seed;
     A[c].key1 = (uint32_t)(seed >> 32);
+    // the planes are the caller's and unchecked: a byte >= q must not
+    // index outside the shared histogram
+    A[c].hist_bins = 256u;
+    A[c].layout = kLayoutU8;
   }
   // the accumulator keeps the previous call's contents: clear what is used
   POTTS_CK(cudaMemsetAsync(rec, 0, (size_t)words * 8, st));

@@ -35,12 +35,20 @@ struct PassArgs {
   uint8_t *own;          // plane being updated (colour `colour`)
   const uint8_t *other;  // the other plane (read only in this pass)
   int32_t L;             // rows
-  int32_t H;             // bytes per row = L / 2 (multiple of 16)
+  int32_t H;             // sites per plane row = L / 2 (multiple of 16)
   uint32_t q;
   uint32_t colour;
   uint32_t t_lo, t_hi;   // global sweep index
   uint32_t key0, key1;   // seed
+  uint32_t layout;       // kLayoutU8 (1) or kLayoutU4 (2)
+  uint32_t hist_bins;    // shared histogram bins: q, or 256 when the planes
+                         // come from the caller unchecked (any byte value
+                         // then indexes inside the histogram)
 };
+
+// Bytes of the shared acceptance table: entry k (dE + 4) at offset 16 k,
+// padded so that any offset byte (0..255) stays inside it.
+constexpr int kTabWords = 65;
 
 // Acceptance rule, tabulated by dE + 4 (0..8).
 //   rule LE  : accept iff a <= tab[dE+4]   (tab = thr-1 for dE >= 1,
@@ -176,20 +184,71 @@ __device__ __forceinline__ void hist_word(uint32_t *lane_hist, uint32_t w) {
   }
 }
 
-__device__ __forceinline__ uint4 ld_stream(const uint8_t *p) {
-  return __ldcs(reinterpret_cast<const uint4 *>(p));
+// ------------------------------------------------------- plane layouts
+// U8: one byte per spin, 16 sites = 16 bytes per thread-row.
+// U4: two spins per byte (site 2b in the low nibble of byte b, site 2b+1 in
+// the high one), 16 sites = 8 bytes, unpacked to the same four byte-words
+// as U8 so that the arithmetic is shared.
+enum { kLayoutU8 = 1, kLayoutU4 = 2 };
+
+// nibbles n0..n7 (sites 0..7) -> bytes [s0..s3], [s4..s7]
+__device__ __forceinline__ void unpack8(uint32_t w, uint32_t &b0,
+                                        uint32_t &b1) {
+  const uint32_t lo = w & 0x0F0F0F0Fu, hi = (w >> 4) & 0x0F0F0F0Fu;
+  b0 = __byte_perm(lo, hi, 0x5140u);
+  b1 = __byte_perm(lo, hi, 0x7362u);
 }
-__device__ __forceinline__ uint4 ld_other(const uint8_t *p) {
-  return __ldg(reinterpret_cast<const uint4 *>(p));
-}
-__device__ __forceinline__ void st_stream(uint8_t *p, uint4 v) {
-  __stcs(reinterpret_cast<uint4 *>(p), v);
+__device__ __forceinline__ uint32_t pack8(uint32_t b0, uint32_t b1) {
+  const uint32_t lo = __byte_perm(b0, b1, 0x6420u);  // s0 s2 s4 s6
+  const uint32_t hi = __byte_perm(b0, b1, 0x7531u);  // s1 s3 s5 s7
+  return lo | (hi << 4);
 }
 
+template <int LAY>
+struct Lay {
+  static constexpr int kChunkBytes = LAY == kLayoutU4 ? 8 : 16;
+  __device__ static __forceinline__ int32_t row_bytes(int32_t H) {
+    return LAY == kLayoutU4 ? H / 2 : H;
+  }
+  __device__ static __forceinline__ void load(const uint8_t *p, bool stream,
+                                              uint32_t w[4]) {
+    if constexpr (LAY == kLayoutU4) {
+      const uint2 v = stream ? __ldcs(reinterpret_cast<const uint2 *>(p))
+                             : __ldg(reinterpret_cast<const uint2 *>(p));
+      unpack8(v.x, w[0], w[1]);
+      unpack8(v.y, w[2], w[3]);
+    } else {
+      const uint4 v = stream ? __ldcs(reinterpret_cast<const uint4 *>(p))
+                             : __ldg(reinterpret_cast<const uint4 *>(p));
+      w[0] = v.x;
+      w[1] = v.y;
+      w[2] = v.z;
+      w[3] = v.w;
+    }
+  }
+  __device__ static __forceinline__ void store(uint8_t *p,
+                                               const uint32_t w[4]) {
+    if constexpr (LAY == kLayoutU4)
+      __stcs(reinterpret_cast<uint2 *>(p),
+             make_uint2(pack8(w[0], w[1]), pack8(w[2], w[3])));
+    else
+      __stcs(reinterpret_cast<uint4 *>(p), make_uint4(w[0], w[1], w[2], w[3]));
+  }
+  // The 4-byte word holding the side site, as a U8 word whose top byte
+  // (LEFT: the site before the window) or low byte (right: the site after
+  // it) is that site.
+  __device__ static __forceinline__ uint32_t edge(uint32_t raw, bool left) {
+    if constexpr (LAY == kLayoutU4)
+      return left ? (raw >> 28) << 24 : raw & 0xFu;
+    else
+      return raw;
+  }
+};
+
 // Per-thread walk state: the three other-plane rows around the current row
-// and the current own row, plus pointers to the next rows.
+// and the current own row (as byte words), plus pointers to the next rows.
 struct Walk {
-  uint4 Up, Ce, S;
+  uint32_t Up[4], Ce[4], S[4];
   const uint8_t *oth_next;  // other plane, row i+1
   const uint8_t *oth_cur;   // other plane, row i
   uint8_t *own_cur;         // own plane, row i
@@ -198,22 +257,29 @@ struct Walk {
 
 // One row: update the 16 sites of the own row i against Up (i-1), Ce (i),
 // the freshly loaded row i+1 and the side byte.  LEFT: the side neighbour
-// is at x-1 (row parity + colour even), else at x+1.
-template <int QB, bool LEFT, bool COUNTS, bool PAIRS, bool LT0>
+// is at x-1 (row parity + colour even), else at x+1.  xb: byte offset of
+// the window in a row; xl, xr: byte offsets of the words holding the side
+// sites; RB: bytes per plane row.
+template <int QB, bool LEFT, bool COUNTS, bool PAIRS, bool LT0, int LAY>
 __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
                                        const uint8_t *tab, Walk &w,
-                                       int32_t x0, int32_t xl, int32_t xr,
-                                       bool more, uint32_t *lane_hist,
+                                       int32_t x0, int32_t xb, int32_t xl,
+                                       int32_t xr, int32_t RB, bool more,
+                                       uint32_t *lane_hist,
                                        uint32_t &ne_acc) {
+  using IO = Lay<LAY>;
   const int32_t L = A.L, H = A.H;
-  const uint4 Dn = ld_other(w.oth_next);
-  const uint32_t ew = __ldg(reinterpret_cast<const uint32_t *>(
-      w.oth_cur - x0 + (LEFT ? xl : xr)));
-  uint8_t *own_next = (w.i + 1 == L) ? A.own + x0 : w.own_cur + H;
-  uint4 Sn = w.S;
-  if (more) Sn = ld_stream(own_next);
+  uint32_t Dw[4];
+  IO::load(w.oth_next, false, Dw);
+  const uint32_t ew = IO::edge(
+      __ldg(reinterpret_cast<const uint32_t *>(w.oth_cur - xb +
+                                               (LEFT ? xl : xr))),
+      LEFT);
+  uint8_t *own_next = (w.i + 1 == L) ? A.own + xb : w.own_cur + RB;
+  uint32_t Sn[4] = {w.S[0], w.S[1], w.S[2], w.S[3]};
+  if (more) IO::load(own_next, true, Sn);
 
-  const uint32_t Cw[4] = {w.Ce.x, w.Ce.y, w.Ce.z, w.Ce.w};
+  const uint32_t *Cw = w.Ce;
   uint32_t Wd[4];
   if (LEFT) {
     Wd[0] = __funnelshift_l(ew, Cw[0], 8);
@@ -226,9 +292,6 @@ __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
     Wd[2] = __funnelshift_r(Cw[2], Cw[3], 8);
     Wd[3] = __funnelshift_r(Cw[3], ew, 8);
   }
-  const uint32_t Uw[4] = {w.Up.x, w.Up.y, w.Up.z, w.Up.w};
-  const uint32_t Dw[4] = {Dn.x, Dn.y, Dn.z, Dn.w};
-  const uint32_t Sw[4] = {w.S.x, w.S.y, w.S.z, w.S.w};
   const uint32_t g0 = (uint32_t)(((int64_t)w.i * H + x0) >> 2);
   uint32_t Nw[4];
 #pragma unroll
@@ -239,11 +302,11 @@ __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
     const uint32_t P = pack4((uint32_t)(r0 >> 32), (uint32_t)(r1 >> 32),
                              (uint32_t)(r2 >> 32), (uint32_t)(r3 >> 32));
     uint32_t no16 = 0;
-    const uint32_t idx = delta_index<QB, COUNTS>(Sw[k], P, Uw[k], Dw[k],
+    const uint32_t idx = delta_index<QB, COUNTS>(w.S[k], P, w.Up[k], Dw[k],
                                                  Cw[k], Wd[k], &no16);
     const uint32_t m = accept_mask<LT0>(idx, (uint32_t)r0, (uint32_t)r1,
                                         (uint32_t)r2, (uint32_t)r3, tab);
-    Nw[k] = (P & m) | (Sw[k] & ~m);
+    Nw[k] = (P & m) | (w.S[k] & ~m);
     if (COUNTS) {
       // unequal neighbours after the update: NE_new where accepted
       const uint32_t nn16 = idx + no16 - 0x40404040u;
@@ -251,45 +314,52 @@ __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
       ne_acc += __umulhi(nf16, 1u << 28);  // += nf16 >> 4 (<= 4 per byte)
     }
   }
-  st_stream(w.own_cur, make_uint4(Nw[0], Nw[1], Nw[2], Nw[3]));
+  IO::store(w.own_cur, Nw);
   if (lane_hist) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) hist_word<PAIRS>(lane_hist, Nw[k]);
   }
   // advance
-  w.Up = w.Ce;
-  w.Ce = Dn;
-  w.S = Sn;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    w.Up[k] = w.Ce[k];
+    w.Ce[k] = Dw[k];
+    w.S[k] = Sn[k];
+  }
   w.oth_cur = w.oth_next;
-  w.oth_next = (w.i + 2 >= L) ? A.other + x0 + (int64_t)(w.i + 2 - L) * H
-                              : w.oth_next + H;
+  w.oth_next = (w.i + 2 >= L) ? A.other + xb + (int64_t)(w.i + 2 - L) * RB
+                              : w.oth_next + RB;
   w.own_cur = own_next;
   w.i += 1;
 }
 
-// Walks rows [i0, i0 + rows) of the 16-byte column starting at byte x0 of
+// Walks rows [i0, i0 + rows) of the 16-site column starting at site x0 of
 // the plane of colour COLOUR.  lane_hist (may be null): per-lane histogram
 // counters of the updated sites.  COUNTS (black pass): *ne_total receives
 // the number of unequal (site, neighbour) pairs after the update.
-template <int QB, int COLOUR, bool COUNTS, bool PAIRS, bool LT0>
+template <int QB, int COLOUR, bool COUNTS, bool PAIRS, bool LT0,
+          int LAY = kLayoutU8>
 __device__ __forceinline__ void walk_column(const PassArgs &A,
                                             const PhiloxKey &ks,
                                             const uint8_t *tab, int32_t x0,
                                             int32_t i0, int32_t rows,
                                             uint32_t *lane_hist,
                                             uint32_t *ne_total) {
+  using IO = Lay<LAY>;
   const int32_t L = A.L, H = A.H;
-  const int32_t xl = (x0 == 0) ? H - 4 : x0 - 4;    // word holding x0-1
-  const int32_t xr = (x0 + 16 == H) ? 0 : x0 + 16;  // word holding x0+16
+  const int32_t RB = IO::row_bytes(H);
+  const int32_t xb = LAY == kLayoutU4 ? x0 / 2 : x0;
+  const int32_t xl = (x0 == 0) ? RB - 4 : xb - 4;  // word holding site x0-1
+  const int32_t xr = (x0 + 16 == H) ? 0 : xb + IO::kChunkBytes;  // x0+16
   Walk w;
   const int32_t im = (i0 == 0) ? L - 1 : i0 - 1;
   const int32_t ip = (i0 + 1 == L) ? 0 : i0 + 1;
-  w.oth_cur = A.other + (int64_t)i0 * H + x0;
-  w.oth_next = A.other + (int64_t)ip * H + x0;
-  w.own_cur = A.own + (int64_t)i0 * H + x0;
-  w.Up = ld_other(A.other + (int64_t)im * H + x0);
-  w.Ce = ld_other(w.oth_cur);
-  w.S = ld_stream(w.own_cur);
+  w.oth_cur = A.other + (int64_t)i0 * RB + xb;
+  w.oth_next = A.other + (int64_t)ip * RB + xb;
+  w.own_cur = A.own + (int64_t)i0 * RB + xb;
+  IO::load(A.other + (int64_t)im * RB + xb, false, w.Up);
+  IO::load(w.oth_cur, false, w.Ce);
+  IO::load(w.own_cur, true, w.S);
   w.i = i0;
   uint32_t ne_acc = 0;
   int32_t r = 0;
@@ -297,11 +367,10 @@ __device__ __forceinline__ void walk_column(const PassArgs &A,
   // rows when rows is even, so pairs of rows have a fixed pattern.
   if ((i0 & 1) == 0) {
     for (; r + 2 <= rows; r += 2) {
-      do_row<QB, COLOUR == 0, COUNTS, PAIRS, LT0>(A, ks, tab, w, x0, xl, xr,
-                                                  true, lane_hist, ne_acc);
-      do_row<QB, COLOUR == 1, COUNTS, PAIRS, LT0>(A, ks, tab, w, x0, xl, xr,
-                                                  r + 2 < rows, lane_hist,
-                                                  ne_acc);
+      do_row<QB, COLOUR == 0, COUNTS, PAIRS, LT0, LAY>(
+          A, ks, tab, w, x0, xb, xl, xr, RB, true, lane_hist, ne_acc);
+      do_row<QB, COLOUR == 1, COUNTS, PAIRS, LT0, LAY>(
+          A, ks, tab, w, x0, xb, xl, xr, RB, r + 2 < rows, lane_hist, ne_acc);
       if (COUNTS) {
         *ne_total += (ne_acc * 0x01010101u) >> 24;
         ne_acc = 0;
@@ -311,11 +380,11 @@ __device__ __forceinline__ void walk_column(const PassArgs &A,
   for (; r < rows; ++r) {
     const bool left = ((w.i + COLOUR) & 1) == 0;
     if (left)
-      do_row<QB, true, COUNTS, PAIRS, LT0>(A, ks, tab, w, x0, xl, xr,
-                                           r + 1 < rows, lane_hist, ne_acc);
+      do_row<QB, true, COUNTS, PAIRS, LT0, LAY>(
+          A, ks, tab, w, x0, xb, xl, xr, RB, r + 1 < rows, lane_hist, ne_acc);
     else
-      do_row<QB, false, COUNTS, PAIRS, LT0>(A, ks, tab, w, x0, xl, xr,
-                                            r + 1 < rows, lane_hist, ne_acc);
+      do_row<QB, false, COUNTS, PAIRS, LT0, LAY>(
+          A, ks, tab, w, x0, xb, xl, xr, RB, r + 1 < rows, lane_hist, ne_acc);
     if (COUNTS) {
       *ne_total += (ne_acc * 0x01010101u) >> 24;
       ne_acc = 0;

@@ -203,3 +203,48 @@ def test_mid_config_protocol(start, ladder_dir):
                           oracle.sweep_sites(pre, q, seed, tidx, b, idx))
     B, hist = oracle.recount(g.spins(), q)
     assert int(rec[0, 0]) == B and np.array_equal(rec[0, 1:], hist)
+
+
+# ------------------------------------------------------- packed 4-bit layout
+U4_CASES = [(32, 2, 1, 0.44, 30), (96, 9, 0, math.log(4.0), 20),
+            (160, 16, 1, 1.3, 15), (544, 15, 1, 1.1, 8), (128, 9, 0, 40.0, 4),
+            (128, 6, 1, 0.0, 4), (4160, 9, 1, workloads.beta_at(9, 1.0), 2)]
+
+
+@pytest.mark.parametrize("L,q,start,beta,sweeps", U4_CASES)
+def test_u4_layout_matches_oracle(L, q, start, beta, sweeps):
+    seed = 77 + L
+    g = potts.Lattice(L, q, start, seed, layout=potts.LAYOUT_U4)
+    o = oracle.Lattice(L, q, start, seed)
+    assert np.array_equal(g.spins(), o.spins())
+    assert np.array_equal(g.sweep(beta, sweeps), o.sweep(beta, sweeps))
+    assert np.array_equal(g.spins(), o.spins())
+    assert g.device_planes()[2] == L // 4
+
+
+def test_u4_equals_u8_and_rejects_large_q():
+    a = potts.Lattice(2048, 12, 1, 3, layout=potts.LAYOUT_U4)
+    b = potts.Lattice(2048, 12, 1, 3, layout=potts.LAYOUT_U8)
+    assert np.array_equal(a.sweep(1.2, 20), b.sweep(1.2, 20))
+    assert np.array_equal(a.spins(), b.spins())
+    spins = workloads.random_spins(256, 16, 9)
+    c = potts.Lattice(256, 16, 0, 4, layout=potts.LAYOUT_U4)
+    c.set_state(spins, 5)
+    assert np.array_equal(c.spins(), spins)
+    with pytest.raises(potts.PottsError) as ei:
+        potts.Lattice(64, 17, 0, 1, layout=potts.LAYOUT_U4)
+    assert ei.value.code == potts.POTTS_EINVAL
+
+
+def test_u4_paper_scale_sampled():
+    L, q, seed = 32768, 9, 11
+    beta = workloads.beta_at(q, 1.0)
+    g = potts.Lattice(L, q, 1, seed, layout=potts.LAYOUT_U4)
+    g.sweep(beta, 2, records=False)
+    pre, t = g.spins(), g.sweep_index
+    rec = g.sweep(beta, 1)
+    idx = np.random.default_rng(3).integers(0, L * L, 200_000, dtype=np.int64)
+    assert np.array_equal(g.spins().ravel()[idx],
+                          oracle.sweep_sites(pre, q, seed, t, beta, idx))
+    B, hist = oracle.recount(g.spins(), q)
+    assert int(rec[0, 0]) == B and np.array_equal(rec[0, 1:], hist)
