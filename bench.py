@@ -48,7 +48,7 @@ sys.path.insert(0, ROOT)
 METRIC = "ns/spin-update @L=32768 q=9 (frac HBM peak)"
 UNIT = "ns/update"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "colour_pass_L16384_q9.md")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "colour_pass_L32768_q9_traffic.md")
 KERNEL_SOURCES = ["pass_u8.cuh", "philox.cuh", "kernels.cu"]
 
 

@@ -39,7 +39,7 @@ constexpr int kPassThreads = 128;
 // Minimum resident CTAs per SM requested from the compiler for the pass
 // kernels (caps registers at 65536 / (128 * POTTS_PASS_MINB) per thread).
 #ifndef POTTS_PASS_MINB
-#define POTTS_PASS_MINB 8
+#define POTTS_PASS_MINB 6
 #endif
 
 TileGeom choose_geom(int32_t L, int32_t H, int32_t q, int32_t sm_count,
