@@ -138,12 +138,17 @@ void Engine::release() {
     sl = Slot();
   }
   drop_units();
-  if (aux_) cudaStreamSynchronize(aux_);
-  if (aux_) cudaStreamDestroy(aux_);
+  for (int l = 0; l < kMaxLanes - 1; ++l) {
+    if (aux_[l]) {
+      cudaStreamSynchronize(aux_[l]);
+      cudaStreamDestroy(aux_[l]);
+    }
+    if (join_[l]) cudaEventDestroy(join_[l]);
+    aux_[l] = nullptr;
+    join_[l] = nullptr;
+  }
   if (fork_) cudaEventDestroy(fork_);
-  if (join_) cudaEventDestroy(join_);
-  aux_ = nullptr;
-  fork_ = join_ = nullptr;
+  fork_ = nullptr;
   if (pool_) cudaMemPoolDestroy(pool_);
   pool_ = nullptr;
 }
@@ -171,9 +176,11 @@ int Engine::init(cudaStream_t stream) {
                                    &keep));
   for (Slot &sl : slots_)
     POTTS_CK(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
-  POTTS_CK(cudaStreamCreateWithFlags(&aux_, cudaStreamNonBlocking));
   POTTS_CK(cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming));
-  POTTS_CK(cudaEventCreateWithFlags(&join_, cudaEventDisableTiming));
+  for (int l = 0; l < kMaxLanes - 1; ++l) {
+    POTTS_CK(cudaStreamCreateWithFlags(&aux_[l], cudaStreamNonBlocking));
+    POTTS_CK(cudaEventCreateWithFlags(&join_[l], cudaEventDisableTiming));
+  }
   return POTTS_OK;
 }
 
@@ -269,11 +276,13 @@ int Engine::rebuild() {
   std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
     return members_[a]->L > members_[b]->L;
   });
-  lanes_ = members_.size() >= 2 ? 2 : 1;
+  lanes_ = (int)std::min<size_t>(kMaxLanes, std::max<size_t>(1, members_.size()));
   std::vector<int> lane_of(members_.size(), 0);
-  double work[2] = {0, 0};
-  for (size_t i : order) {
-    const int l = (lanes_ == 2 && work[1] < work[0]) ? 1 : 0;
+  double work[kMaxLanes] = {};
+  for (size_t i : order) {  // biggest first, onto the least loaded lane
+    int l = 0;
+    for (int k = 1; k < lanes_; ++k)
+      if (work[k] < work[l]) l = k;
     lane_of[i] = l;
     work[l] += (double)members_[i]->L * members_[i]->L;
   }
@@ -327,19 +336,20 @@ int Engine::rebuild() {
 
 int Engine::launch_all(Slot &sl, int32_t kmax) {
   POTTS_CK(cudaMemsetAsync(sl.d_rec, 0, sl.rec_used * 8, st_));
-  if (lanes_ == 2) {  // fork the second lane
+  if (lanes_ > 1) {  // fork the extra lanes
     POTTS_CK(cudaEventRecord(fork_, st_));
-    POTTS_CK(cudaStreamWaitEvent(aux_, fork_, 0));
+    for (int l = 1; l < lanes_; ++l)
+      POTTS_CK(cudaStreamWaitEvent(aux_[l - 1], fork_, 0));
   }
   for (int32_t s = 0; s < kmax; ++s)
     for (int c = 0; c < 2; ++c)
       for (const Unit &u : units_)
         POTTS_CK(launch_batch_pass(*u.P, u.lt0, sl.d_step, c, s,
                                    (size_t)u.maxq * 32 * sizeof(uint32_t),
-                                   u.lane ? aux_ : st_));
-  if (lanes_ == 2) {  // join
-    POTTS_CK(cudaEventRecord(join_, aux_));
-    POTTS_CK(cudaStreamWaitEvent(st_, join_, 0));
+                                   u.lane ? aux_[u.lane - 1] : st_));
+  for (int l = 1; l < lanes_; ++l) {  // join
+    POTTS_CK(cudaEventRecord(join_[l - 1], aux_[l - 1]));
+    POTTS_CK(cudaStreamWaitEvent(st_, join_[l - 1], 0));
   }
   return POTTS_OK;
 }

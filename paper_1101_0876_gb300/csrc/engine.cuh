@@ -13,6 +13,13 @@
 
 #include "internal.cuh"
 
+// Stream lanes of a batched step: members are split into this many groups of
+// about equal work, each on its own stream, so that one group's pass tail
+// overlaps another group's work.
+#ifndef POTTS_ENGINE_LANES
+#define POTTS_ENGINE_LANES 2
+#endif
+
 namespace potts {
 
 // Per-member data that stays fixed while the membership does not change.
@@ -122,7 +129,7 @@ class Engine {
     LaunchParams *P = nullptr;
     bool lt0 = false;
     int32_t maxq = 2;
-    int lane = 0;             // stream lane (0: st_, 1: aux_)
+    int lane = 0;             // stream lane (0: st_, l > 0: aux_[l-1])
   };
   struct Slot {               // buffers of one in-flight step
     StepDesc *d_step = nullptr, *h_step = nullptr;
@@ -143,8 +150,10 @@ class Engine {
   void drop_units();
 
   cudaStream_t st_ = nullptr;
-  cudaStream_t aux_ = nullptr;   // second lane, forked from st_ per step
-  cudaEvent_t fork_ = nullptr, join_ = nullptr;
+  // extra lanes, forked from st_ and joined back every step
+  static constexpr int kMaxLanes = POTTS_ENGINE_LANES;
+  cudaStream_t aux_[kMaxLanes - 1] = {};
+  cudaEvent_t fork_ = nullptr, join_[kMaxLanes - 1] = {};
   int lanes_ = 1;
   cudaMemPool_t pool_ = nullptr;
   int sm_count_ = 1;
