@@ -9,12 +9,44 @@
 namespace potts {
 
 // ------------------------------------------------------------- kernel
-// One CTA per row tile.  The CTA finds its member by a binary search over
-// the tile offsets in the parameter block (uniform), then runs exactly the
-// walk, Philox counters and reductions of the single-lattice pass on that
-// tile, into the member's record of sweep s.  Members whose step has fewer
+// A member's colour pass is split into work items: item w walks the TR rows
+// [rg*TR, rg*TR + TR) of the 16-site column chunk c, with c = w mod nchunks
+// and rg = w div nchunks.  CTA b of the member takes items [128 b, 128 b +
+// 128), one per thread, so every thread of every CTA but the member's last
+// has a walk, whatever the row width.  The CTA finds its member by a binary
+// search over the tile offsets in the parameter block (uniform), then runs
+// exactly the walk, Philox counters and reductions of the single-lattice
+// pass, into the member's record of sweep s.  Members whose step has fewer
 // than s+1 sweeps return at once.
 constexpr int32_t kEngineTR = 32;
+
+// Rows per walk for a member: the longest power of two up to tr_max whose
+// items fill at least 7/8 of the member's CTA slots (L rows, nchunks chunks
+// per row), else the one that fills most.  Short walks cost one extra
+// other-plane row load per walk; a half-empty last CTA costs idle lanes.
+int32_t engine_walk_rows(int32_t L, int32_t nchunks, int32_t tr_max) {
+  int32_t tr = 1;
+  while (tr * 2 <= tr_max) tr *= 2;
+  int32_t best = 1;
+  double best_fill = -1.0;
+  for (; tr >= 1; tr >>= 1) {
+    const int64_t items = (int64_t)nchunks * ((L + tr - 1) / tr);
+    const int64_t slots = (items + kPassThreads - 1) / kPassThreads *
+                          kPassThreads * tr;
+    const double fill = (double)L * nchunks / (double)slots;
+    if (fill >= 0.875) return tr;
+    if (fill > best_fill) {
+      best_fill = fill;
+      best = tr;
+    }
+  }
+  return best;
+}
+
+int32_t engine_tiles(int32_t L, int32_t nchunks, int32_t tr) {
+  const int64_t items = (int64_t)nchunks * ((L + tr - 1) / tr);
+  return (int32_t)((items + kPassThreads - 1) / kPassThreads);
+}
 
 #ifndef POTTS_BATCH_MINB
 #define POTTS_BATCH_MINB 4
@@ -61,13 +93,12 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_BATCH_MINB)
   A.hist_bins = q;
   A.layout = kLayoutU8;
   const PhiloxKey ks = philox_schedule(A.key0, A.key1);
-  const int32_t lt = bid - d.tile0;
-  const int32_t tx = lt % d.gx, ty = lt / d.gx;
-  const int32_t cx = (int32_t)tid % d.CX, rg = (int32_t)tid / d.CX;
-  const int32_t chunk = tx * d.CX + cx;
-  const int32_t i0 = (ty * d.RG + rg) * d.TR;
+  const int32_t item = (bid - d.tile0) * kPassThreads + (int32_t)tid;
+  const int32_t rg = item / d.nchunks;
+  const int32_t chunk = item - rg * d.nchunks;
+  const int32_t i0 = rg * d.TR;
   uint32_t ne = 0, rows = 0;
-  if (rg < d.RG && chunk * 16 < d.H && i0 < d.L) {
+  if (i0 < d.L) {
     rows = (uint32_t)min(d.TR, d.L - i0);
     const uint8_t *tab = reinterpret_cast<const uint8_t *>(s_tab);
     uint32_t *lh = s_hist + (tid & 31u);
@@ -261,12 +292,9 @@ int Engine::slot_capacity(Slot &sl, int32_t k) {
   return POTTS_OK;
 }
 
-// Groups the members by acceptance rule into launches of at most
-// kMaxMembersPerLaunch members, biggest lattices first, and lays out their
-// row tiles (one CTA each).
 // Splits the members into two lanes of about equal work (sites), biggest
 // lattices first, and each lane by acceptance rule into launches of at most
-// kMaxMembersPerLaunch members; lays out their row tiles (one CTA each).
+// kMaxMembersPerLaunch members; lays out their work items (128 per CTA).
 // The lanes run on two streams, so the tail of one lane's pass overlaps
 // the other lane's work.
 int Engine::rebuild() {
@@ -286,10 +314,17 @@ int Engine::rebuild() {
     lane_of[i] = l;
     work[l] += (double)members_[i]->L * members_[i]->L;
   }
+  // inside a launch, members of one spin-width class (one walk variant of
+  // the kernel) are contiguous, biggest first within the class, so that the
+  // CTAs resident on an SM at a time mostly run the same code
+  std::vector<size_t> placed(order);
+  std::stable_sort(placed.begin(), placed.end(), [&](size_t a, size_t b) {
+    return qbits_for(members_[a]->q) < qbits_for(members_[b]->q);
+  });
   for (int lane = 0; lane < lanes_; ++lane) {
     for (int rule = 0; rule < 2; ++rule) {
       Unit u;
-      for (size_t i : order) {
+      for (size_t i : placed) {
         if (member_lt0_[i] != rule || lane_of[i] != lane) continue;
         if (!u.P || u.P->n == kMaxMembersPerLaunch) {
           if (u.P) units_.push_back(u);
@@ -301,11 +336,12 @@ int Engine::rebuild() {
         }
         Member *m = members_[i];
         const int32_t H = m->L / 2;
-        // walks of kEngineTR rows by default: many lattices share the
-        // device, so each tile should carry enough sites to amortise its
+        // walks of up to kEngineTR rows by default: many lattices share
+        // the device, so each CTA should carry enough sites to amortise its
         // histogram set-up instead of spreading one lattice over every SM
-        const TileGeom g = choose_geom(m->L, H, m->q, sm_count_,
-                                       m->TR > 0 ? m->TR : kEngineTR);
+        const int32_t nchunks = H / 16;
+        const int32_t tr = engine_walk_rows(
+            m->L, nchunks, m->TR > 0 ? m->TR : kEngineTR);
         StaticDesc &d = u.P->m[u.P->n];
         d.plane[0] = m->planes;
         d.plane[1] = m->planes + m->plane_bytes;
@@ -315,13 +351,12 @@ int Engine::rebuild() {
         d.qbits = qbits_for(m->q);
         d.key0 = (uint32_t)m->seed;
         d.key1 = (uint32_t)(m->seed >> 32);
-        d.CX = g.CX;
-        d.RG = g.RG;
-        d.TR = g.TR;
-        d.gx = g.gx;
+        d.nchunks = nchunks;
+        d.TR = tr;
         d.tile0 = u.P->ntiles;
+        d.pad = 0;
         d.step = (int32_t)i;
-        u.P->ntiles += g.gx * g.ty;
+        u.P->ntiles += engine_tiles(m->L, nchunks, tr);
         u.P->n += 1;
         u.maxq = std::max(u.maxq, m->q);
       }

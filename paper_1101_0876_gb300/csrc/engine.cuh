@@ -1,7 +1,8 @@
 // Batched sweep engine: many independent lattices of different L, q, beta
 // and seed advanced together.  Each colour pass of every member runs in one
-// launch with one CTA per row tile of every member (members are found from
-// the CTA index through the launch's parameter block); a step of k sweeps
+// launch (per stream lane and acceptance rule) whose CTAs each take 128 of
+// a member's column walks (members are found from the CTA index through the
+// launch's parameter block); a step of k sweeps
 // (2k launches plus the zeroing of the step's records) is captured in one
 // CUDA graph and replayed while the membership does not change.  Used by
 // the batch API and by the serving loop.
@@ -29,8 +30,10 @@ struct StaticDesc {
   uint8_t *plane[2];          // white, black
   int32_t L, H, q, qbits;
   uint32_t key0, key1;        // seed
-  int32_t CX, RG, TR, gx;     // row-tile shape; gx tiles per row band
+  int32_t nchunks;            // 16-site column chunks per plane row (H/16)
+  int32_t TR;                 // rows per walk
   int32_t tile0;              // first tile (CTA) of this member in the launch
+  int32_t pad;
   int32_t step;               // index of its StepDesc
 };
 
