@@ -23,7 +23,8 @@ Metric: ns per spin update (time / (N * sweeps)), whole job, lower is better.
   roofline  the colour-pass kernel against measured HBM bandwidth, 1.5 bytes
             per spin per pass (read own plane, write own plane, read other
             plane once) = 3 bytes per spin per sweep.
-  cpu_baseline  the serial CPU oracle on a bounded sample (one core).
+  cpu_baseline  the serial CPU oracle on a bounded sample (one core), plus
+                one oracle instance per host core (aggregate).
 
 With torchrun (N > 1) each rank sweeps its own replica (weak scaling, no
 data-path collective); the time is the max over ranks.
@@ -204,6 +205,32 @@ def cpu_oracle_ns_per_update(L: int, q: int, beta: float, sweeps: int,
     return dt * 1e9 / (L * L * sweeps), dt
 
 
+def _cpu_oracle_worker(a):
+    L, q, beta, sweeps, seed = a
+    import oracle
+    lat = oracle.Lattice(L, q, 1, seed)
+    lat.sweep(beta, 1, records=False)
+    t0 = time.perf_counter()
+    lat.sweep(beta, sweeps)
+    return L * L * sweeps, time.perf_counter() - t0
+
+
+def cpu_oracle_all_cores(L: int, q: int, beta: float, sweeps: int,
+                         seed: int):
+    """One independent oracle instance per host core (processes started
+    with spawn), each sweeping its own L x L lattice; aggregate updates/s
+    over the slowest worker's time."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    jobs = [(L, q, beta, sweeps, seed + i) for i in range(n)]
+    with cf.ProcessPoolExecutor(n, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_cpu_oracle_worker, jobs))
+    upd = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    return upd / wall, n, wall
+
+
 # --------------------------------------------------------- our arm
 def run_ours(args):
     import numpy as np
@@ -348,6 +375,14 @@ def run_ours(args):
             "sample": f"serial oracle, L={Lc} q={q} random start at T_c, "
                       f"{sweeps} sweeps ({dt:.1f} s); per-update cost of the "
                       f"serial raster loop does not depend on L"}
+        ups, ncores, wall = cpu_oracle_all_cores(512, q, betas[1],
+                                                 args.cpu_sweeps_all, cfg.seed)
+        line["cpu_baseline"]["all_cores"] = {
+            "value": 1e9 / ups, "unit": UNIT, "updates_per_s": ups,
+            "cores": ncores,
+            "sample": f"{ncores} independent serial oracles (one process "
+                      f"per core), each L=512 q={q} random start at T_c, "
+                      f"{args.cpu_sweeps_all} sweeps ({wall:.1f} s)"}
     return line
 
 
@@ -520,6 +555,8 @@ def main():
     ap.add_argument("--no-job", action="store_true")
     ap.add_argument("--cpu-L", type=int, default=2048)
     ap.add_argument("--cpu-sweeps", type=int, default=40)
+    ap.add_argument("--cpu-sweeps-all", type=int, default=24,
+                    help="sweeps per core of the all-cores oracle baseline")
     ap.add_argument("--ref-L", type=int, default=1024)
     ap.add_argument("--no-u4", action="store_true")
     ap.add_argument("--no-batched", action="store_true")

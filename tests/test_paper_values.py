@@ -4,7 +4,8 @@ import os
 
 import pytest
 
-from paper_1101_0876_gb300.analysis import exact_energies, latent_heat
+from paper_1101_0876_gb300.analysis import (exact_energies, latent_heat,
+                                            magnetization_jump_series)
 from paper_1101_0876_gb300.workloads import beta_at, tc
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden",
@@ -48,3 +49,14 @@ def test_latent_heat_limits():
     # q -> infinity: e_o -> -2, e_d -> 0
     e_o, e_d = exact_energies(10**8)
     assert abs(e_o + 2.0) < 1e-3 and abs(e_d) < 1e-3
+
+
+@pytest.mark.parametrize("row", _rows("exact_dm"))
+def test_exact_dm_column_is_the_truncated_series(row):
+    """The "exact" Delta m column equals the printed series (Eq. 8) with
+    five subtracted terms, and neither four nor six terms give it."""
+    q, val = row
+    assert round(magnetization_jump_series(q, 5), 6) == pytest.approx(val, abs=1e-12)
+    if q < 50:
+        assert round(magnetization_jump_series(q, 4), 6) != val
+        assert round(magnetization_jump_series(q, 6), 6) != val
