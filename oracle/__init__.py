@@ -1,5 +1,6 @@
 """Serial CPU oracle for the checkerboard Metropolis sweep of the 2D q-state
-Potts model (Ferrero et al., Sec. 2.1, Sec. 3, Sec. 3.3-3.4, Sec. 5).
+Potts model (Ferrero et al., Sec. 2.1, Sec. 3, Sec. 3.3-3.4, Sec. 5), and of
+the heat-bath variant (one of the single-flip algorithms Sec. 6 proposes).
 
 TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()``
 and the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may load
@@ -84,6 +85,19 @@ def lib() -> ctypes.CDLL:
                                         ctypes.c_int32, ctypes.c_uint64,
                                         ctypes.c_int64, i64p, u8p]
         L.oracle_init_sites.restype = ctypes.c_int
+        L.oracle_heatbath_weights.argtypes = [
+            ctypes.c_double, ctypes.c_int32, u64p,
+            ctypes.POINTER(ctypes.c_int32)]
+        L.oracle_heatbath_weights.restype = ctypes.c_int
+        L.oracle_sweep_ex.argtypes = [ctypes.c_void_p, ctypes.c_double,
+                                      ctypes.c_int64, u64p, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_int32]
+        L.oracle_sweep_ex.restype = ctypes.c_int
+        L.oracle_sweep_sites_ex.argtypes = [
+            u8p, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+            ctypes.c_uint64, ctypes.c_double, ctypes.c_int64, i64p, u8p,
+            ctypes.c_int32]
+        L.oracle_sweep_sites_ex.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -115,6 +129,22 @@ def thresholds(beta: float) -> np.ndarray:
     return out
 
 
+METROPOLIS, HEATBATH = 0, 1
+
+
+def heatbath_weights(beta: float, q: int):
+    """(W[0..4], m) of the heat-bath rule; ValueError when beta is out of
+    range."""
+    W = np.zeros(5, dtype=np.uint64)
+    m = ctypes.c_int32()
+    rc = lib().oracle_heatbath_weights(float(beta), int(q),
+                                       _ptr(W, ctypes.c_uint64),
+                                       ctypes.byref(m))
+    if rc != 0:
+        raise ValueError(f"no heat-bath weights for beta={beta!r}, q={q}")
+    return W, int(m.value)
+
+
 def recount(spins: np.ndarray, q: int):
     """(B, hist) of an L x L row-major uint8 lattice, from the definition."""
     s = np.ascontiguousarray(spins, dtype=np.uint8)
@@ -128,17 +158,17 @@ def recount(spins: np.ndarray, q: int):
 
 
 def sweep_sites(pre: np.ndarray, q: int, seed: int, sweep: int, beta: float,
-                idx: np.ndarray) -> np.ndarray:
+                idx: np.ndarray, update: int = METROPOLIS) -> np.ndarray:
     """Values after sweep `sweep` of the sites idx (= i*L + j), computed one
     by one from the pre-sweep lattice `pre`."""
     s = np.ascontiguousarray(pre, dtype=np.uint8)
     L = s.shape[0]
     ix = np.ascontiguousarray(idx, dtype=np.int64)
     out = np.zeros(ix.size, dtype=np.uint8)
-    rc = lib().oracle_sweep_sites(_ptr(s, ctypes.c_uint8), L, q, seed, sweep,
-                                  float(beta), ix.size,
-                                  _ptr(ix, ctypes.c_int64),
-                                  _ptr(out, ctypes.c_uint8))
+    rc = lib().oracle_sweep_sites_ex(_ptr(s, ctypes.c_uint8), L, q, seed,
+                                     sweep, float(beta), ix.size,
+                                     _ptr(ix, ctypes.c_int64),
+                                     _ptr(out, ctypes.c_uint8), int(update))
     if rc != 0:
         raise ValueError("oracle_sweep_sites: bad arguments")
     return out
@@ -173,13 +203,14 @@ class Lattice:
             self._h = None
 
     def sweep(self, beta: float, nsweeps: int, order: int = 0,
-              check: bool = False, records: bool = True):
+              check: bool = False, records: bool = True,
+              update: int = METROPOLIS):
         out = (np.zeros((nsweeps, 1 + self.q), dtype=np.uint64)
                if records else None)
         ptr = (_ptr(out, ctypes.c_uint64) if records
                else ctypes.POINTER(ctypes.c_uint64)())
-        rc = lib().oracle_sweep(self._h, float(beta), int(nsweeps), ptr,
-                                order, 1 if check else 0)
+        rc = lib().oracle_sweep_ex(self._h, float(beta), int(nsweeps), ptr,
+                                   order, 1 if check else 0, int(update))
         if rc == -2:
             raise AssertionError("incremental counts differ from a recount")
         if rc != 0:

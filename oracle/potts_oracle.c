@@ -19,6 +19,12 @@
  *     fly); a check mode recounts both from scratch after every sweep.
  * Random numbers: Philox4x32-10 (Salmon et al., SC'11), one call per group
  * of four consecutive sites of one colour, one 32-bit word per site.
+ *
+ * Also a heat-bath single-spin update (one of the other single-flip
+ * algorithms Sec. 6 proposes for this lattice code): the new spin is drawn
+ * from the site's conditional Boltzmann distribution given its four
+ * neighbours, by inverting an integer cumulative distribution with the same
+ * 32-bit word per site.
  */
 #include "potts_oracle.h"
 
@@ -87,6 +93,58 @@ int oracle_thresholds(double beta, uint64_t thr[5]) {
     thr[d] = (uint64_t)floor(ldexp(p, 32));
   }
   return 0;
+}
+
+/* ---------------------------------------------------------------------
+ * Heat-bath weights.  Given its four neighbours, a site takes state x with
+ * probability exp(beta n_x) / sum_y exp(beta n_y), n_x = number of
+ * neighbours in state x (H = -sum delta, Eq. 1).  Integer form:
+ * W[n] = round(2^m exp(beta n)) for n = 0..4, so W[0] = 2^m, with m the
+ * largest integer in 0..31 for which the normaliser Z = sum_x W[n_x] stays
+ * below 2^32 for every way the four neighbours can split into states.
+ * ------------------------------------------------------------------- */
+
+/* Largest Z over the splits of four neighbours into k distinct states with
+ * counts c_1..c_k: Z = sum W[c] + (q - k) W[0]. */
+static uint64_t heatbath_zmax(const uint64_t w[5], int32_t q) {
+  static const int splits[5][4] = {
+      {4, 0, 0, 0}, {3, 1, 0, 0}, {2, 2, 0, 0}, {2, 1, 1, 0}, {1, 1, 1, 1}};
+  uint64_t zmax = 0;
+  for (int p = 0; p < 5; ++p) {
+    int k = 0;
+    uint64_t z = 0;
+    for (int c = 0; c < 4; ++c) {
+      if (splits[p][c] == 0) continue;
+      z += w[splits[p][c]];
+      k += 1;
+    }
+    if (k > q) continue;  /* fewer states than classes: impossible split */
+    z += (uint64_t)(q - k) * w[0];
+    if (z > zmax) zmax = z;
+  }
+  return zmax;
+}
+
+int oracle_heatbath_weights(double beta, int32_t q, uint64_t W[5],
+                            int32_t *m_out) {
+  if (!(beta >= 0.0) || !isfinite(beta) || q < 2 || q > 256) return -1;
+  for (int32_t m = 31; m >= 0; --m) {
+    uint64_t w[5];
+    int fits = 1;
+    for (int n = 0; n <= 4; ++n) {
+      double x = ldexp(exp(beta * (double)n), m);
+      if (!(x < 4294967296.0)) {
+        fits = 0;
+        break;
+      }
+      w[n] = (uint64_t)floor(x + 0.5);
+    }
+    if (!fits || heatbath_zmax(w, q) > 0xFFFFFFFFull) continue;
+    memcpy(W, w, sizeof w);
+    *m_out = m;
+    return 0;
+  }
+  return -1;  /* beta too large for 32-bit weights */
 }
 
 /* ---------------------------------------------------------------------
@@ -162,15 +220,91 @@ static void neighbours(const uint8_t *s, int32_t L, int32_t i, int32_t j,
   nb[3] = s[(int64_t)i * L + wrap(j + 1, L)];
 }
 
-/* One Metropolis trial at (i,j) during the pass of colour c of sweep t. */
-static int metropolis_site(const uint8_t *s, int32_t L, int32_t q,
-                           uint64_t seed, uint64_t t, int c,
-                           const uint64_t thr[5], int32_t i, int32_t j,
-                           int *dB) {
+/* The single-site heat-bath rule.  nb[0..3] are the neighbours (up, down,
+ * left, right), u the site's 32-bit word.  The q states are laid out on
+ * [0, Z): first the distinct neighbour states in the order they first
+ * appear in nb, each with width W[count], then the states no neighbour
+ * holds, in increasing order, each with width W[0] = 2^m.  The new spin is
+ * the state whose interval holds r = floor(u Z / 2^32).  Returns it and
+ * stores the change of B (neighbours equal to the new spin minus those
+ * equal to the old one) in *dB. */
+static int heatbath_rule(int old, const int nb[4], uint32_t u, int32_t q,
+                         const uint64_t W[5], int32_t m, int *dB) {
+  int cls[4], cnt[4], k = 0;
+  for (int a = 0; a < 4; ++a) {
+    int seen = -1;
+    for (int b = 0; b < k; ++b)
+      if (cls[b] == nb[a]) seen = b;
+    if (seen >= 0) {
+      cnt[seen] += 1;
+    } else {
+      cls[k] = nb[a];
+      cnt[k] = 1;
+      k += 1;
+    }
+  }
+  uint64_t Z = (uint64_t)(q - k) * W[0];
+  for (int b = 0; b < k; ++b) Z += W[cnt[b]];
+  uint64_t r = ((uint64_t)u * Z) >> 32;
+  int now = -1;
+  for (int b = 0; b < k && now < 0; ++b) {
+    if (r < W[cnt[b]])
+      now = cls[b];
+    else
+      r -= W[cnt[b]];
+  }
+  if (now < 0) {
+    uint64_t idx = r >> m;  /* which of the q - k unheld states */
+    for (int x = 0; x < q && now < 0; ++x) {
+      int held = 0;
+      for (int a = 0; a < 4; ++a) held |= nb[a] == x;
+      if (held) continue;
+      if (idx == 0)
+        now = x;
+      else
+        idx -= 1;
+    }
+  }
+  int n_old = 0, n_now = 0;
+  for (int a = 0; a < 4; ++a) {
+    n_old += nb[a] == old;
+    n_now += nb[a] == now;
+  }
+  *dB = n_now - n_old;
+  return now;
+}
+
+/* The update rule of a sweep: Metropolis (thr) or heat bath (W, m). */
+typedef struct {
+  int32_t heatbath;
+  uint64_t thr[5];
+  uint64_t W[5];
+  int32_t m;
+} update_rule;
+
+static int rule_setup(update_rule *ur, int32_t update, double beta,
+                      int32_t q) {
+  memset(ur, 0, sizeof *ur);
+  if (update == 0) return oracle_thresholds(beta, ur->thr);
+  if (update != 1) return -1;
+  ur->heatbath = 1;
+  return oracle_heatbath_weights(beta, q, ur->W, &ur->m);
+}
+
+static int apply_rule(const update_rule *ur, int old, const int nb[4],
+                      uint32_t u, int32_t q, int *dB) {
+  if (ur->heatbath) return heatbath_rule(old, nb, u, q, ur->W, ur->m, dB);
+  return metropolis_rule(old, nb, u, q, ur->thr, dB);
+}
+
+/* One trial at (i,j) during the pass of colour c of sweep t. */
+static int update_site(const uint8_t *s, int32_t L, int32_t q,
+                       uint64_t seed, uint64_t t, int c,
+                       const update_rule *ur, int32_t i, int32_t j, int *dB) {
   int nb[4];
   neighbours(s, L, i, j, nb);
   uint32_t u = oracle_site_word(seed, t, (uint32_t)c, colour_index(L, i, j));
-  return metropolis_rule(s[(int64_t)i * L + j], nb, u, q, thr, dB);
+  return apply_rule(ur, s[(int64_t)i * L + j], nb, u, q, dB);
 }
 
 /* Initial spin of site (i,j).  Ordered start: 0 (the paper's s_i = 1,
@@ -227,9 +361,15 @@ void oracle_destroy(oracle_lattice *lat) {
 
 int oracle_sweep(oracle_lattice *lat, double beta, int64_t nsweeps,
                  uint64_t *out_counts, int32_t order, int32_t check) {
-  uint64_t thr[5];
+  return oracle_sweep_ex(lat, beta, nsweeps, out_counts, order, check, 0);
+}
+
+int oracle_sweep_ex(oracle_lattice *lat, double beta, int64_t nsweeps,
+                    uint64_t *out_counts, int32_t order, int32_t check,
+                    int32_t update) {
+  update_rule ur;
   if (!lat || nsweeps < 0 || (order != 0 && order != 1)) return -1;
-  if (oracle_thresholds(beta, thr) != 0) return -1;
+  if (rule_setup(&ur, update, beta, lat->q) != 0) return -1;
   const int32_t L = lat->L, q = lat->q;
   uint64_t *tmp_hist = NULL;
   if (check) {
@@ -245,8 +385,7 @@ int oracle_sweep(oracle_lattice *lat, double beta, int64_t nsweeps,
         if (((i + j) & 1) != c) continue;
         int dB = 0;
         int old = lat->s[lin];
-        int now = metropolis_site(lat->s, L, q, lat->seed, t, c, thr, i, j,
-                                  &dB);
+        int now = update_site(lat->s, L, q, lat->seed, t, c, &ur, i, j, &dB);
         if (now != old) {
           lat->hist[old] -= 1;
           lat->hist[now] += 1;
@@ -297,39 +436,47 @@ void oracle_counts(const oracle_lattice *lat, uint64_t *B, uint64_t *hist) {
 }
 
 /* A site's value after the white pass of sweep t: white sites take one
- * Metropolis step against the pre-sweep black spins, black sites keep
- * their value.  Valid for even L, where same-coloured sites never touch. */
+ * update step against the pre-sweep black spins, black sites keep their
+ * value.  Valid for even L, where same-coloured sites never touch. */
 static int after_white(const uint8_t *pre, int32_t L, int32_t q,
-                       uint64_t seed, uint64_t t, const uint64_t thr[5],
+                       uint64_t seed, uint64_t t, const update_rule *ur,
                        int32_t i, int32_t j) {
   int dB;
   if (((i + j) & 1) != 0) return pre[(int64_t)i * L + j];
-  return metropolis_site(pre, L, q, seed, t, 0, thr, i, j, &dB);
+  return update_site(pre, L, q, seed, t, 0, ur, i, j, &dB);
 }
 
 int oracle_sweep_sites(const uint8_t *pre, int32_t L, int32_t q,
                        uint64_t seed, uint64_t sweep, double beta,
                        int64_t nsites, const int64_t *idx, uint8_t *out) {
-  uint64_t thr[5];
+  return oracle_sweep_sites_ex(pre, L, q, seed, sweep, beta, nsites, idx, out,
+                               0);
+}
+
+int oracle_sweep_sites_ex(const uint8_t *pre, int32_t L, int32_t q,
+                          uint64_t seed, uint64_t sweep, double beta,
+                          int64_t nsites, const int64_t *idx, uint8_t *out,
+                          int32_t update) {
+  update_rule ur;
   if ((L & 1) != 0 || L < 4 || q < 2 || q > 256) return -1;
-  if (oracle_thresholds(beta, thr) != 0) return -1;
+  if (rule_setup(&ur, update, beta, q) != 0) return -1;
   for (int64_t n = 0; n < nsites; ++n) {
     int64_t lin = idx[n];
     if (lin < 0 || lin >= (int64_t)L * L) return -1;
     int32_t i = (int32_t)(lin / L), j = (int32_t)(lin % L);
     if (((i + j) & 1) == 0) {
-      out[n] = (uint8_t)after_white(pre, L, q, seed, sweep, thr, i, j);
+      out[n] = (uint8_t)after_white(pre, L, q, seed, sweep, &ur, i, j);
       continue;
     }
     /* Black site: its four white neighbours as they are after the white
-     * pass, then one Metropolis step against them. */
+     * pass, then one update step against them. */
     int nb[4], dB;
     const int32_t ni[4] = {wrap(i - 1, L), wrap(i + 1, L), i, i};
     const int32_t nj[4] = {j, j, wrap(j - 1, L), wrap(j + 1, L)};
     for (int m = 0; m < 4; ++m)
-      nb[m] = after_white(pre, L, q, seed, sweep, thr, ni[m], nj[m]);
+      nb[m] = after_white(pre, L, q, seed, sweep, &ur, ni[m], nj[m]);
     uint32_t u = oracle_site_word(seed, sweep, 1u, colour_index(L, i, j));
-    out[n] = (uint8_t)metropolis_rule(pre[lin], nb, u, q, thr, &dB);
+    out[n] = (uint8_t)apply_rule(&ur, pre[lin], nb, u, q, &dB);
   }
   return 0;
 }

@@ -1,6 +1,6 @@
 /*
- * Serial CPU oracle for the checkerboard Metropolis sweep of the 2D q-state
- * Potts model (Ferrero, De Francesco, Wolovick, Cannas, "q-state Potts model
+ * Serial CPU oracle for the checkerboard Metropolis (and heat-bath) sweep of
+ * the 2D q-state Potts model (Ferrero, De Francesco, Wolovick, Cannas, "q-state Potts model
  * metastability study using optimized GPU-based Monte Carlo algorithms").
  *
  * TEST INFRASTRUCTURE ONLY.  This code is the reference that the CUDA path is
@@ -38,6 +38,14 @@ uint32_t oracle_site_word(uint64_t seed, uint64_t sweep, uint32_t domain,
  * Returns 0, or -1 when beta is negative or not finite. */
 int oracle_thresholds(double beta, uint64_t thr[5]);
 
+/* Heat-bath weights W[n] = round(2^m exp(beta n)), n = 0..4 (W[0] = 2^m),
+ * with m the largest integer in 0..31 that keeps every normaliser
+ * Z = sum over the q states of W[#neighbours in that state] below 2^32.
+ * Returns 0, or -1 for a bad beta or q, or when no m >= 0 fits (beta too
+ * large for 32-bit weights). */
+int oracle_heatbath_weights(double beta, int32_t q, uint64_t W[5],
+                            int32_t *m);
+
 /* Full recount of the satisfied-bond number B (Eq. 1 with J = 1 gives
  * H = -B) and of the q-state histogram, straight from the definition. */
 void oracle_recount(const uint8_t *s, int32_t L, int32_t q, uint64_t *B,
@@ -64,6 +72,13 @@ void oracle_destroy(oracle_lattice *lat);
 int oracle_sweep(oracle_lattice *lat, double beta, int64_t nsweeps,
                  uint64_t *out_counts, int32_t order, int32_t check);
 
+/* As oracle_sweep, with the update rule chosen: update 0 = Metropolis,
+ * 1 = heat bath (oracle_heatbath_weights; -1 when beta is out of its
+ * range). */
+int oracle_sweep_ex(oracle_lattice *lat, double beta, int64_t nsweeps,
+                    uint64_t *out_counts, int32_t order, int32_t check,
+                    int32_t update);
+
 /* Copies the current spins (L*L bytes, row-major) out / in.  set_state also
  * sets the global sweep index and recomputes B and the histogram. */
 void oracle_get_spins(const oracle_lattice *lat, uint8_t *out);
@@ -78,6 +93,10 @@ void oracle_counts(const oracle_lattice *lat, uint64_t *B, uint64_t *hist);
 int oracle_sweep_sites(const uint8_t *pre, int32_t L, int32_t q,
                        uint64_t seed, uint64_t sweep, double beta,
                        int64_t nsites, const int64_t *idx, uint8_t *out);
+int oracle_sweep_sites_ex(const uint8_t *pre, int32_t L, int32_t q,
+                          uint64_t seed, uint64_t sweep, double beta,
+                          int64_t nsites, const int64_t *idx, uint8_t *out,
+                          int32_t update);
 
 #ifdef __cplusplus
 }

@@ -5,7 +5,8 @@ Each case rewrites one spot of oracle/potts_oracle.c in a temporary copy,
 builds it, and runs the pin meant to catch it: PyTorch's Philox engine for
 the generator and its counter layout, exact enumeration for the Metropolis
 rule and the threshold table, the incremental-vs-recount check for the
-bookkeeping, the colour-independence check for the random start.
+bookkeeping, the colour-independence check for the random start, and for
+the heat bath its conditional-Boltzmann outcome distribution and the recount.
 """
 import ctypes
 import os
@@ -49,6 +50,16 @@ MUTATIONS = {
                          "recount"),
     "random_start_domain": ("oracle_site_word(seed, 0, 2u + (uint32_t)c,",
                             "oracle_site_word(seed, 0, 2u,", "random_start"),
+    # heat bath
+    "hb_weights_half_beta": (
+        "      double x = ldexp(exp(beta * (double)n), m);",
+        "      double x = ldexp(exp(0.5 * beta * (double)n), m);",
+        "hb_distribution"),
+    "hb_unheld_states_include_held": (
+        "      for (int a = 0; a < 4; ++a) held |= nb[a] == x;",
+        "      for (int a = 0; a < 4; ++a) held |= 0;", "hb_distribution"),
+    "hb_dB_sign": ("  *dB = n_now - n_old;", "  *dB = n_old - n_now;",
+                   "hb_recount"),
 }
 
 
@@ -76,6 +87,14 @@ def _build(tmp_path, name, old, new):
                                  ctypes.c_int32]
     lib.oracle_get_spins.argtypes = [ctypes.c_void_p,
                                      ctypes.POINTER(ctypes.c_uint8)]
+    lib.oracle_sweep_ex.argtypes = [ctypes.c_void_p, ctypes.c_double,
+                                    ctypes.c_int64, P64, ctypes.c_int32,
+                                    ctypes.c_int32, ctypes.c_int32]
+    lib.oracle_sweep_sites_ex.argtypes = [
+        ctypes.POINTER(ctypes.c_uint8), ctypes.c_int32, ctypes.c_int32,
+        ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int64,
+        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint8),
+        ctypes.c_int32]
     return lib
 
 
@@ -138,6 +157,38 @@ def _random_start_pin(lib):
     return np.mean(s[par == 0] == s[par == 1]) < 0.2
 
 
+def _hb_distribution_pin(lib):
+    """Heat-bath outcomes of white sites whose neighbours are (0, 0, 1, 1)
+    against exp(beta n_x) / sum_y exp(beta n_y)."""
+    L, q, beta = 16, 5, 1.3
+    pre = np.zeros((L, L), np.uint8)
+    pre[1::2, 0::2] = 0       # up/down neighbours of white (even, even) sites
+    pre[0::2, 1::2] = 1       # left/right neighbours
+    ii, jj = np.meshgrid(np.arange(0, L, 2), np.arange(0, L, 2), indexing="ij")
+    idx = (ii * L + jj).ravel().astype(np.int64)
+    c = np.zeros(q, np.int64)
+    out = np.zeros(idx.size, np.uint8)
+    for t in range(200):
+        rc = lib.oracle_sweep_sites_ex(
+            pre.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), L, q, 3, t,
+            beta, idx.size, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+            out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), 1)
+        assert rc == 0
+        c += np.bincount(out, minlength=q)[:q]
+    p = np.exp(beta * np.array([2, 2, 0, 0, 0.0]))
+    p /= p.sum()
+    n = c.sum()
+    return float(((c - n * p) ** 2 / (n * p)).sum()) < 3 * (q - 1) + 25
+
+
+def _hb_recount_pin(lib):
+    h = lib.oracle_create(12, 5, 1, 3)
+    rc = lib.oracle_sweep_ex(h, 0.8, 40, ctypes.POINTER(ctypes.c_uint64)(),
+                             0, 1, 1)
+    lib.oracle_destroy(h)
+    return rc == 0
+
+
 def test_unmutated_copy_passes_every_pin(tmp_path, torch_philox, brute_force):
     lib = _build(tmp_path, "clean", "#define PHILOX_M0",
                  "#define PHILOX_M0")
@@ -146,6 +197,8 @@ def test_unmutated_copy_passes_every_pin(tmp_path, torch_philox, brute_force):
     assert _enumeration_pin(lib, brute_force)
     assert _recount_pin(lib)
     assert _random_start_pin(lib)
+    assert _hb_distribution_pin(lib)
+    assert _hb_recount_pin(lib)
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
@@ -158,5 +211,7 @@ def test_planted_mistake_is_caught(tmp_path, torch_philox, brute_force, name):
         "enumeration": lambda: _enumeration_pin(lib, brute_force),
         "recount": lambda: _recount_pin(lib),
         "random_start": lambda: _random_start_pin(lib),
+        "hb_distribution": lambda: _hb_distribution_pin(lib),
+        "hb_recount": lambda: _hb_recount_pin(lib),
     }[pin]()
     assert not passed, f"pin '{pin}' did not catch mutation '{name}'"
