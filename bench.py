@@ -25,6 +25,7 @@ Metric: ns per spin update (time / (N * sweeps)), whole job, lower is better.
             plane once) = 3 bytes per spin per sweep.
   cpu_baseline  the serial CPU oracle on a bounded sample (one core), plus
                 one oracle instance per host core (aggregate).
+  heatbath      the same workload with the heat-bath update rule.
 
 With torchrun (N > 1) each rank sweeps its own replica (weak scaling, no
 data-path collective); the time is the max over ranks.
@@ -361,6 +362,9 @@ def run_ours(args):
     if ws == 1 and not args.no_u4:
         lat.close()
         line["u4"] = measure_u4(args, L, q, betas)
+    if ws == 1 and not args.no_heatbath:
+        lat.close()
+        line["heatbath"] = measure_heatbath(args, L, q, betas)
     if ws == 1 and not args.no_batched:
         lat.close()
         line["batched"] = measure_batched(args, line["updates_per_s"])
@@ -412,6 +416,35 @@ def measure_u4(args, L, q, betas):
     return {"value": ms * 1e6 / (N * n), "unit": UNIT, "sweeps": n,
             "updates_per_s": N * n / (ms * 1e-3),
             "bytes_per_update": 1.5, "achieved_gbs": gbs,
+            "frac_hbm": gbs / hbm}
+
+
+# ------------------------------------------------------ heat-bath rule
+def measure_heatbath(args, L, q, betas):
+    """The same workload with the heat-bath update (U8), device-timed like
+    `value`; same 3 bytes per site per sweep."""
+    import torch
+    from paper_1101_0876_gb300 import potts
+    stream = torch.cuda.Stream()
+    lat = potts.Lattice(L, q, potts.START_RANDOM, 11)
+    lat.set_update(potts.UPDATE_HEATBATH)
+    lat.set_stream(stream.cuda_stream)
+    lat.sweep(betas[0], 3, records=False)
+    n = max(3, args.steps // 4)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.sweep(betas[1], n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    lat.close()
+    N = L * L
+    hbm, _ = measured_peaks()
+    gbs = 3.0 * N * n / (ms * 1e-3) / 1e9
+    return {"value": ms * 1e6 / (N * n), "unit": UNIT, "sweeps": n,
+            "updates_per_s": N * n / (ms * 1e-3), "achieved_gbs": gbs,
             "frac_hbm": gbs / hbm}
 
 
@@ -559,6 +592,7 @@ def main():
                     help="sweeps per core of the all-cores oracle baseline")
     ap.add_argument("--ref-L", type=int, default=1024)
     ap.add_argument("--no-u4", action="store_true")
+    ap.add_argument("--no-heatbath", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--batch-sweeps", type=int, default=500)

@@ -134,6 +134,33 @@ int potts_set_state(potts_h h, const uint8_t *LxL, uint64_t sweep);
  * Errors: EINVAL for beta < 0 or not finite. */
 int potts_threshold_table(double beta, uint64_t out_thr[5]);
 
+/* Single-site update rule of potts_sweep on a handle.
+ *   POTTS_UPDATE_METROPOLIS (default): the rule above (Sec. 2.2, Sec. 3.2).
+ *   POTTS_UPDATE_HEATBATH: heat bath, one of the other single-flip
+ *     algorithms Sec. 6 proposes: the new spin is drawn from the site's
+ *     conditional Boltzmann distribution given its four neighbours,
+ *     P(x) = W[n_x] / Z, n_x = neighbours in state x, with the integer
+ *     weights of potts_heatbath_weights, by inverting the cumulative
+ *     distribution at r = floor(u Z / 2^32) with the site's Philox word u
+ *     (same counters as Metropolis).  The states are laid out on [0, Z):
+ *     first the distinct neighbour states in the order they first appear
+ *     among (up, down, left, right), each of width W[count], then the states
+ *     no neighbour holds in increasing order, each of width W[0].
+ * Records and observables are the same for both rules.  The rule applies to
+ * later potts_sweep calls; a beta outside the heat-bath weights' range then
+ * fails with EINVAL.  Errors: EINVAL (unknown rule). */
+enum { POTTS_UPDATE_METROPOLIS = 0, POTTS_UPDATE_HEATBATH = 1 };
+int potts_set_update(potts_h h, int32_t update);
+
+/* Heat-bath weights for beta and q: out_W[n] = round(2^m exp(beta n)) for
+ * n = 0..4 (so out_W[0] = 2^m), computed on the host in FP64, with *out_m
+ * the largest m in 0..31 that keeps the normaliser Z = sum over the q
+ * states of W[neighbours in that state] below 2^32 for every neighbour
+ * configuration.  Errors: EINVAL for beta < 0 or not finite, q outside
+ * 2..256, or beta so large that exp(4 beta) + q - 1 >= 2^32. */
+int potts_heatbath_weights(double beta, int32_t q, uint64_t out_W[5],
+                           int32_t *out_m);
+
 /* Makes the handle run on `stream` (a cudaStream_t, or NULL for the
  * handle's own stream).  The caller keeps ownership of the stream. */
 int potts_set_stream(potts_h h, void *stream);

@@ -1,0 +1,206 @@
+// Heat-bath colour pass: the same plane layout, walk, Philox words and
+// reductions as the Metropolis pass (pass_u8.cuh), with the single-site
+// rule replaced.  Heat bath is one of the other single-flip algorithms the
+// paper proposes for this lattice code (Sec. 6).
+//
+// Rule.  Given its four neighbours (up, down, left, right), a site takes
+// state x with probability W[n_x] / Z, n_x = number of neighbours in state
+// x, W[n] = round(2^m exp(beta n)) (W[0] = 2^m exactly), Z = sum over the q
+// states.  The states are laid out on [0, Z): first the distinct neighbour
+// states in the order they first appear in (up, down, left, right), each of
+// width W[count], then the states no neighbour holds, in increasing order,
+// each of width 2^m; the new spin is the state whose interval holds
+// r = floor(u Z / 2^32), u the site's Philox word.  The host picks m so that
+// Z < 2^32 for every neighbour configuration, so all of it is 32-bit.
+#pragma once
+#include <cstdint>
+
+#include "pass_u8.cuh"
+
+namespace potts {
+
+// W[0..4] as above, W[5..7] = 0: the index of a neighbour that repeats an
+// earlier one, so its class has no width of its own.
+struct HeatTable {
+  uint32_t W[8];
+  uint32_t m;
+};
+
+__device__ __forceinline__ void hb_cswap(uint32_t &a, uint32_t &b) {
+  const uint32_t lo = min(a, b), hi = max(a, b);
+  a = lo;
+  b = hi;
+}
+
+// New spin of one site.  t0..t3: neighbours (up, down, left, right); u: the
+// site's word; sW: the table in shared memory.
+__device__ __forceinline__ uint32_t hb_site(uint32_t t0, uint32_t t1,
+                                            uint32_t t2, uint32_t t3,
+                                            uint32_t u, uint32_t q,
+                                            const uint32_t *sW, uint32_t m) {
+  const uint32_t e01 = t0 == t1, e02 = t0 == t2, e03 = t0 == t3;
+  const uint32_t e12 = t1 == t2, e13 = t1 == t3, e23 = t2 == t3;
+  // first appearances of a state among the neighbours
+  const bool f1 = !e01, f2 = !(e02 | e12), f3 = !(e03 | e13 | e23);
+  const uint32_t w0 = sW[1 + e01 + e02 + e03];
+  const uint32_t w1 = sW[f1 ? 1 + e12 + e13 : 5];
+  const uint32_t w2 = sW[f2 ? 1 + e23 : 5];
+  const uint32_t w3 = sW[f3 ? 1 : 5];
+  const uint32_t k = 1u + f1 + f2 + f3;  // distinct neighbour states
+  const uint32_t s1 = w0, s2 = s1 + w1, s3 = s2 + w2, s4 = s3 + w3;
+  const uint32_t Z = s4 + (q - k) * sW[0];
+  const uint32_t r = __umulhi(u, Z);
+  // states no neighbour holds: the idx-th of them in increasing order is idx
+  // moved past every held state at or below it (held states sorted; a
+  // repeated neighbour is replaced by 256, above every state)
+  uint32_t d0 = t0, d1 = f1 ? t1 : 256u, d2 = f2 ? t2 : 256u,
+           d3 = f3 ? t3 : 256u;
+  hb_cswap(d0, d1);
+  hb_cswap(d2, d3);
+  hb_cswap(d0, d2);
+  hb_cswap(d1, d3);
+  hb_cswap(d1, d2);
+  uint32_t s = (r - s4) >> m;
+  s += d0 <= s;
+  s += d1 <= s;
+  s += d2 <= s;
+  s += d3 <= s;
+  s = r < s4 ? t3 : s;
+  s = r < s3 ? t2 : s;
+  s = r < s2 ? t1 : s;
+  s = r < s1 ? t0 : s;
+  // s < q already; the clamp keeps the shared histogram in bounds whatever
+  // the spins in memory hold
+  return min(s, q - 1u);
+}
+
+__device__ __forceinline__ uint32_t hb_byte(uint32_t w, int b) {
+  return __byte_perm(w, 0u, 0x4440u + (uint32_t)b);
+}
+
+// One row of 16 sites (the Metropolis do_row with the heat-bath rule).
+template <bool LEFT, bool COUNTS, bool PAIRS, int LAY>
+__device__ __forceinline__ void hb_row(const PassArgs &A, const PhiloxKey &ks,
+                                       const uint32_t *sW, uint32_t m,
+                                       Walk &w, int32_t x0, int32_t xb,
+                                       int32_t xl, int32_t xr, int32_t RB,
+                                       bool more, uint32_t *lane_hist,
+                                       uint32_t &ne_acc) {
+  using IO = Lay<LAY>;
+  const int32_t L = A.L, H = A.H;
+  uint32_t Dw[4];
+  IO::load(w.oth_next, false, Dw);
+  const uint32_t ew = IO::edge(
+      __ldg(reinterpret_cast<const uint32_t *>(w.oth_cur - xb +
+                                               (LEFT ? xl : xr))),
+      LEFT);
+  uint8_t *own_next = (w.i + 1 == L) ? A.own + xb : w.own_cur + RB;
+  uint32_t Sn[4] = {w.S[0], w.S[1], w.S[2], w.S[3]};
+  if (more) IO::load(own_next, true, Sn);
+  const uint32_t *Cw = w.Ce;
+  uint32_t Wd[4];
+  if (LEFT) {
+    Wd[0] = __funnelshift_l(ew, Cw[0], 8);
+    Wd[1] = __funnelshift_l(Cw[0], Cw[1], 8);
+    Wd[2] = __funnelshift_l(Cw[1], Cw[2], 8);
+    Wd[3] = __funnelshift_l(Cw[2], Cw[3], 8);
+  } else {
+    Wd[0] = __funnelshift_r(Cw[0], Cw[1], 8);
+    Wd[1] = __funnelshift_r(Cw[1], Cw[2], 8);
+    Wd[2] = __funnelshift_r(Cw[2], Cw[3], 8);
+    Wd[3] = __funnelshift_r(Cw[3], ew, 8);
+  }
+  const uint32_t g0 = (uint32_t)(((int64_t)w.i * H + x0) >> 2);
+  uint32_t Nw[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint4 u = philox10(g0 + (uint32_t)k, A.t_lo, A.colour, A.t_hi, ks);
+    const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
+    // left / right neighbours: the window byte x-1 (Wd) and x (Cw) when the
+    // side neighbour is at x-1, else x (Cw) and x+1 (Wd)
+    const uint32_t Lw = LEFT ? Wd[k] : Cw[k];
+    const uint32_t Rw = LEFT ? Cw[k] : Wd[k];
+    uint32_t s[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      s[b] = hb_site(hb_byte(w.Up[k], b), hb_byte(Dw[k], b),
+                     hb_byte(Lw, b), hb_byte(Rw, b), uw[b], A.q, sW, m);
+    Nw[k] = pack4(s[0], s[1], s[2], s[3]);
+    if (COUNTS) {
+      // 16 x (neighbours unequal to the new spin) per byte
+      const uint32_t nf16 = ne16_sum4<8>(Nw[k] ^ w.Up[k], Nw[k] ^ Dw[k],
+                                         Nw[k] ^ Cw[k], Nw[k] ^ Wd[k]);
+      ne_acc += __umulhi(nf16, 1u << 28);
+    }
+  }
+  IO::store(w.own_cur, Nw);
+  if (lane_hist) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) hist_word<PAIRS>(lane_hist, Nw[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    w.Up[k] = w.Ce[k];
+    w.Ce[k] = Dw[k];
+    w.S[k] = Sn[k];
+  }
+  w.oth_cur = w.oth_next;
+  w.oth_next = (w.i + 2 >= L) ? A.other + xb + (int64_t)(w.i + 2 - L) * RB
+                              : w.oth_next + RB;
+  w.own_cur = own_next;
+  w.i += 1;
+}
+
+// walk_column with the heat-bath rule.
+template <int COLOUR, bool COUNTS, bool PAIRS, int LAY>
+__device__ __forceinline__ void hb_walk_column(
+    const PassArgs &A, const PhiloxKey &ks, const uint32_t *sW, uint32_t m,
+    int32_t x0, int32_t i0, int32_t rows, uint32_t *lane_hist,
+    uint32_t *ne_total) {
+  using IO = Lay<LAY>;
+  const int32_t L = A.L, H = A.H;
+  const int32_t RB = IO::row_bytes(H);
+  const int32_t xb = LAY == kLayoutU4 ? x0 / 2 : x0;
+  const int32_t xl = (x0 == 0) ? RB - 4 : xb - 4;
+  const int32_t xr = (x0 + 16 == H) ? 0 : xb + IO::kChunkBytes;
+  Walk w;
+  const int32_t im = (i0 == 0) ? L - 1 : i0 - 1;
+  const int32_t ip = (i0 + 1 == L) ? 0 : i0 + 1;
+  w.oth_cur = A.other + (int64_t)i0 * RB + xb;
+  w.oth_next = A.other + (int64_t)ip * RB + xb;
+  w.own_cur = A.own + (int64_t)i0 * RB + xb;
+  IO::load(A.other + (int64_t)im * RB + xb, false, w.Up);
+  IO::load(w.oth_cur, false, w.Ce);
+  IO::load(w.own_cur, true, w.S);
+  w.i = i0;
+  uint32_t ne_acc = 0;
+  int32_t r = 0;
+  if ((i0 & 1) == 0) {
+    for (; r + 2 <= rows; r += 2) {
+      hb_row<COLOUR == 0, COUNTS, PAIRS, LAY>(A, ks, sW, m, w, x0, xb, xl, xr,
+                                              RB, true, lane_hist, ne_acc);
+      hb_row<COLOUR == 1, COUNTS, PAIRS, LAY>(A, ks, sW, m, w, x0, xb, xl, xr,
+                                              RB, r + 2 < rows, lane_hist,
+                                              ne_acc);
+      if (COUNTS) {
+        *ne_total += (ne_acc * 0x01010101u) >> 24;
+        ne_acc = 0;
+      }
+    }
+  }
+  for (; r < rows; ++r) {
+    const bool left = ((w.i + COLOUR) & 1) == 0;
+    if (left)
+      hb_row<true, COUNTS, PAIRS, LAY>(A, ks, sW, m, w, x0, xb, xl, xr, RB,
+                                       r + 1 < rows, lane_hist, ne_acc);
+    else
+      hb_row<false, COUNTS, PAIRS, LAY>(A, ks, sW, m, w, x0, xb, xl, xr, RB,
+                                        r + 1 < rows, lane_hist, ne_acc);
+    if (COUNTS) {
+      *ne_total += (ne_acc * 0x01010101u) >> 24;
+      ne_acc = 0;
+    }
+  }
+}
+
+}  // namespace potts

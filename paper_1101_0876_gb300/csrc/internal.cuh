@@ -53,6 +53,12 @@ int qbits_for(int32_t q);
 bool threshold_table(double beta, uint64_t thr[5]);
 AcceptTable accept_table(const uint64_t thr[5]);
 
+// Heat-bath weights (host FP64, glibc exp): W[n] = round(2^m exp(beta n)),
+// n = 0..4, m the largest in 0..31 keeping every normaliser below 2^32.
+struct HeatTable;
+bool heatbath_table(double beta, int32_t q, uint64_t W[5], int32_t *m);
+HeatTable heat_table(const uint64_t W[5], int32_t m);
+
 // ----------------------------------------------------------- launches
 // One colour pass of one lattice.  rec (may be null) receives, added
 // atomically, the histogram of the updated sites and, on the black pass, B;
@@ -60,6 +66,10 @@ AcceptTable accept_table(const uint64_t thr[5]);
 cudaError_t launch_pass(const PassArgs &A, const AcceptTable &T,
                         const TileGeom &G, unsigned long long *rec,
                         cudaStream_t st);
+// The same colour pass with the heat-bath rule (heatbath.cuh).
+cudaError_t launch_pass_hb(const PassArgs &A, const HeatTable &T,
+                           const TileGeom &G, unsigned long long *rec,
+                           cudaStream_t st);
 // Random start of one plane of plane_sites sites: s = floor(u q / 2^32),
 // u = Philox word of domain 2 + colour at sweep 0.
 cudaError_t launch_init_random(uint8_t *plane, int64_t plane_sites,

@@ -6,6 +6,7 @@
 #include <new>
 #include <vector>
 
+#include "heatbath.cuh"
 #include "internal.cuh"
 
 namespace potts {
@@ -148,6 +149,7 @@ struct potts_lattice {
   int64_t rec_cap = 0;
   TileGeom geom{};
   potts_obs obs{};
+  int32_t update = POTTS_UPDATE_METROPOLIS;
 };
 
 static constexpr int64_t kRecordBytesTarget = 4 << 20;
@@ -267,6 +269,17 @@ int potts_sweep(potts_h h, double beta, int64_t nsweeps, uint64_t *out_counts) {
     return fail(POTTS_EINVAL, "beta must be finite and >= 0 (got %g)", beta);
   const AcceptTable T = accept_table(thr);
   const int32_t q = h->q;
+  const bool hb = h->update == POTTS_UPDATE_HEATBATH;
+  HeatTable HT{};
+  if (hb) {
+    uint64_t W[5];
+    int32_t m = 0;
+    if (!heatbath_table(beta, q, W, &m))
+      return fail(POTTS_EINVAL,
+                  "beta=%g is outside the heat-bath weights' range for q=%d",
+                  beta, q);
+    HT = heat_table(W, m);
+  }
   const int64_t rec_len = 1 + q;
   PassArgs A[2];
   for (int c = 0; c < 2; ++c) {
@@ -290,8 +303,12 @@ int potts_sweep(potts_h h, double beta, int64_t nsweeps, uint64_t *out_counts) {
       for (int c = 0; c < 2; ++c) {
         A[c].t_lo = (uint32_t)t;
         A[c].t_hi = (uint32_t)(t >> 32);
-        POTTS_CK(launch_pass(A[c], T, h->geom, h->d_rec + s * rec_len,
-                             h->stream));
+        if (hb)
+          POTTS_CK(launch_pass_hb(A[c], HT, h->geom, h->d_rec + s * rec_len,
+                                  h->stream));
+        else
+          POTTS_CK(launch_pass(A[c], T, h->geom, h->d_rec + s * rec_len,
+                               h->stream));
       }
     }
     POTTS_CK(cudaMemcpyAsync(h->h_rec, h->d_rec, (size_t)(n * rec_len * 8),
@@ -306,6 +323,14 @@ int potts_sweep(potts_h h, double beta, int64_t nsweeps, uint64_t *out_counts) {
     done += n;
   }
   h->obs.sweep = h->sweep;
+  return POTTS_OK;
+}
+
+int potts_set_update(potts_h h, int32_t update) {
+  if (!h) return fail(POTTS_EINVAL, "handle is NULL");
+  if (update != POTTS_UPDATE_METROPOLIS && update != POTTS_UPDATE_HEATBATH)
+    return fail(POTTS_EINVAL, "unknown update rule %d", update);
+  h->update = update;
   return POTTS_OK;
 }
 

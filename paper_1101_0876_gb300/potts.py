@@ -16,6 +16,7 @@ POTTS_OK, POTTS_EINVAL, POTTS_ENOMEM, POTTS_ECUDA = 0, 1, 2, 3
 POTTS_ETIMEOUT, POTTS_EBUSY, POTTS_ECANCELLED, POTTS_ENOTFOUND = 4, 5, 6, 7
 START_ORDERED, START_RANDOM = 0, 1
 LAYOUT_AUTO, LAYOUT_U8, LAYOUT_U4 = 0, 1, 2
+UPDATE_METROPOLIS, UPDATE_HEATBATH = 0, 1
 
 _u8p = ctypes.POINTER(ctypes.c_uint8)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -76,6 +77,10 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_void_p)]),
     "potts_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double,
                                    ctypes.c_int64, _u64p]),
+    "potts_set_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "potts_heatbath_weights": (ctypes.c_int, [
+        ctypes.c_double, ctypes.c_int32, _u64p,
+        ctypes.POINTER(ctypes.c_int32)]),
     "potts_observables": (ctypes.c_int, [ctypes.c_void_p,
                                          ctypes.POINTER(PottsObs)]),
     "potts_reset_averages": (ctypes.c_int, [ctypes.c_void_p]),
@@ -159,6 +164,16 @@ def _ptr(a: np.ndarray, ct):
     return a.ctypes.data_as(ctypes.POINTER(ct))
 
 
+def heatbath_weights(beta: float, q: int):
+    """(W[0..4], m) of the heat-bath rule for beta and q."""
+    W = np.zeros(5, dtype=np.uint64)
+    m = ctypes.c_int32()
+    check(lib().potts_heatbath_weights(float(beta), int(q),
+                                       _ptr(W, ctypes.c_uint64),
+                                       ctypes.byref(m)))
+    return W, int(m.value)
+
+
 def threshold_table(beta: float) -> np.ndarray:
     out = np.zeros(5, dtype=np.uint64)
     check(lib().potts_threshold_table(float(beta), _ptr(out, ctypes.c_uint64)))
@@ -224,6 +239,11 @@ class Lattice:
             p = ctypes.POINTER(ctypes.c_uint64)()
         check(lib().potts_sweep(self._h, float(beta), int(nsweeps), p))
         return out
+
+    def set_update(self, update: int) -> None:
+        """UPDATE_METROPOLIS (default) or UPDATE_HEATBATH for later
+        sweeps."""
+        check(lib().potts_set_update(self._h, int(update)))
 
     def observables(self) -> dict:
         o = PottsObs()

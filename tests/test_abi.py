@@ -59,6 +59,24 @@ def test_threshold_table_rejects_bad_beta(libpotts):
         assert "beta" in libpotts.last_error()
 
 
+def test_heatbath_weights_equal_oracle(libpotts):
+    rng = np.random.default_rng(12)
+    cases = [(b, q) for q in (2, 3, 9, 15, 24, 96, 200, 256)
+             for b in [0.0, 1e-7, 0.5, np.log1p(np.sqrt(q)), 2.0, 4.0, 5.5]]
+    cases += [(float(b), int(q)) for b, q in
+              zip(rng.uniform(0, 5.6, 300), rng.integers(2, 257, 300))]
+    for b, q in cases:
+        try:
+            Wo, mo = oracle.heatbath_weights(b, q)
+        except ValueError:
+            with pytest.raises(libpotts.PottsError) as ei:
+                libpotts.heatbath_weights(b, q)
+            assert ei.value.code == libpotts.POTTS_EINVAL
+            continue
+        W, m = libpotts.heatbath_weights(b, q)
+        assert m == mo and np.array_equal(W, Wo), (b, q)
+
+
 def test_create_validates_before_touching_the_device(libpotts):
     bad = [(48, 9, 0), (16, 9, 0), (64, 1, 0), (64, 257, 0), (64, 9, 2),
            (65536 + 32, 9, 0)]
