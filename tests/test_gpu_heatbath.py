@@ -105,3 +105,23 @@ def test_full_size_sampled(L, q, layout):
     assert np.array_equal(post.ravel()[idx], expect)
     B, hist = oracle.recount(post, q)
     assert int(rec[0, 0]) == B and np.array_equal(rec[0, 1:], hist)
+
+
+@pytest.mark.parametrize("q,t_over_tc", [(9, 0.95), (9, 1.05), (24, 1.1)])
+def test_heatbath_and_metropolis_sample_the_same_ensemble(q, t_over_tc):
+    """Both rules leave the Boltzmann distribution invariant, so long-run
+    <e> and <m> agree within their statistical errors (L = 256, away from
+    the transition so both relax quickly)."""
+    from paper_1101_0876_gb300.analysis import batch_means, energy_magnetization
+    L = 256
+    beta = workloads.beta_at(q, t_over_tc)
+    res = {}
+    for rule in (potts.UPDATE_METROPOLIS, HB):
+        g = potts.Lattice(L, q, 0 if t_over_tc < 1 else 1, 40 + rule)
+        g.set_update(rule)
+        g.sweep(beta, 3000, records=False)
+        e, m = energy_magnetization(g.sweep(beta, 20000), L, q)
+        res[rule] = (batch_means(e, 50), batch_means(m, 50))
+    for k in range(2):
+        (a, ea), (b, eb) = res[potts.UPDATE_METROPOLIS][k], res[HB][k]
+        assert abs(a - b) < 5 * math.hypot(ea, eb) + 1e-6, (k, a, b, ea, eb)
