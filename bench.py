@@ -270,16 +270,21 @@ def run_ours(args):
     # ---- device-timed region
     barrier(ws)
     torch.cuda.synchronize(dev)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
+    # each temperature's steps in two halves, an event at every boundary:
+    # the per-part times give a median over six repetitions beside the total
+    parts = [(b, h) for b, n in zip(betas, seg) for h in (n // 2, n - n // 2)
+             if h > 0]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)]
+    evs[0].record(stream)
     off = 0
-    for b, n in zip(betas, seg):
+    for (b, n), ev in zip(parts, evs[1:]):
         lat.sweep(b, n, out=recbuf[off:off + n])
         off += n
-    ev1.record(stream)
+        ev.record(stream)
     torch.cuda.synchronize(dev)
-    dev_ms = ev0.elapsed_time(ev1)
+    dev_ms = evs[0].elapsed_time(evs[-1])
+    part_ms = [evs[i].elapsed_time(evs[i + 1]) / n
+               for i, (_, n) in enumerate(parts)]
     barrier(ws)
     dev_ms_max = reduce_max(dev_ms, ws, dev)
 
@@ -335,6 +340,11 @@ def run_ours(args):
         "steps": K,
         "warmup": W,
         "ms_per_step": dev_ms_max / K,
+        "repeats": {"n": len(part_ms),
+                    "ms_per_step": [round(x, 5) for x in part_ms],
+                    "median_ms_per_step": float(np.median(part_ms)),
+                    "note": "the timed steps in six consecutive parts (two "
+                            "per temperature), CUDA events between parts"},
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
@@ -588,7 +598,7 @@ def main():
     ap.add_argument("--no-job", action="store_true")
     ap.add_argument("--cpu-L", type=int, default=2048)
     ap.add_argument("--cpu-sweeps", type=int, default=40)
-    ap.add_argument("--cpu-sweeps-all", type=int, default=24,
+    ap.add_argument("--cpu-sweeps-all", type=int, default=300,
                     help="sweeps per core of the all-cores oracle baseline")
     ap.add_argument("--ref-L", type=int, default=1024)
     ap.add_argument("--no-u4", action="store_true")

@@ -216,6 +216,10 @@ int potts_batch_create(int32_t n, const int32_t *L, const int32_t *q,
  * room for nsweeps * (1 + q_i) uint64 records of lattice i. */
 int potts_batch_sweep(potts_batch_h b, const double *beta, int64_t nsweeps,
                       uint64_t *const *out_counts);
+/* update[n]: the single-site rule of each lattice for later sweeps
+ * (POTTS_UPDATE_METROPOLIS, the default, or POTTS_UPDATE_HEATBATH; see
+ * potts_set_update).  Errors: EINVAL (unknown rule). */
+int potts_batch_set_update(potts_batch_h b, const int32_t *update);
 int potts_batch_get_spins(potts_batch_h b, int32_t i, uint8_t *out_LxL);
 int potts_batch_observables(potts_batch_h b, int32_t i, potts_obs *out);
 int potts_batch_destroy(potts_batch_h b);
@@ -239,7 +243,7 @@ typedef struct {
 
 typedef struct {
   int32_t L, q, start;
-  int32_t reserved;
+  int32_t update;   /* POTTS_UPDATE_METROPOLIS (0) or POTTS_UPDATE_HEATBATH */
   double beta;
   int64_t nsweeps;
   uint64_t seed;

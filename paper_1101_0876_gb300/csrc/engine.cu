@@ -1,10 +1,12 @@
 // Batched sweep engine (see engine.cuh) and the potts_batch_* entry points.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cstring>
 #include <new>
 
 #include "engine.cuh"
+#include "heatbath.cuh"
 
 namespace potts {
 
@@ -52,11 +54,14 @@ int32_t engine_tiles(int32_t L, int32_t nchunks, int32_t tr) {
 #define POTTS_BATCH_MINB 4
 #endif
 
-template <int COLOUR, bool LT0>
-__global__ void __launch_bounds__(kPassThreads, POTTS_BATCH_MINB)
+// The heat-bath walk keeps more values live: 3 resident CTAs (no spills).
+template <int COLOUR, int KIND>
+__global__ void __launch_bounds__(kPassThreads,
+                                  KIND == kKindHB ? 3 : POTTS_BATCH_MINB)
     batch_pass_kernel(const __grid_constant__ LaunchParams P,
                       const StepDesc *__restrict__ S, int32_t s) {
   constexpr bool COUNTS = COLOUR == 1;
+  constexpr bool LT0 = KIND == kKindLT0;
   extern __shared__ uint32_t s_hist[];
   __shared__ __align__(16) uint32_t s_tab[kTabWords];
   __shared__ uint32_t s_sat;
@@ -72,8 +77,12 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_BATCH_MINB)
   const StepDesc &sd = S[d.step];
   if (s >= sd.nsweeps) return;  // same for the whole CTA
   const uint32_t q = (uint32_t)d.q;
-  for (uint32_t i = tid; i < (uint32_t)kTabWords; i += kPassThreads)
-    s_tab[i] = (i % 4u == 0 && i / 4u < 9u) ? sd.tab[i / 4u] : 0u;
+  if (KIND == kKindHB) {
+    if (tid < 8) s_tab[tid] = sd.tab[tid];  // W[0..7]
+  } else {
+    for (uint32_t i = tid; i < (uint32_t)kTabWords; i += kPassThreads)
+      s_tab[i] = (i % 4u == 0 && i / 4u < 9u) ? sd.tab[i / 4u] : 0u;
+  }
   for (uint32_t v = tid; v < q * 32u; v += kPassThreads) s_hist[v] = 0;
   if (tid == 0) s_sat = 0;
   __syncthreads();
@@ -103,7 +112,10 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_BATCH_MINB)
     const uint8_t *tab = reinterpret_cast<const uint8_t *>(s_tab);
     uint32_t *lh = s_hist + (tid & 31u);
     const int32_t x0 = chunk * 16;
-    switch (d.qbits) {
+    if (KIND == kKindHB) {
+      hb_walk_column<COLOUR, COUNTS, false, kLayoutU8>(
+          A, ks, s_tab, sd.tab[8], x0, i0, (int)rows, lh, &ne);
+    } else switch (d.qbits) {
       case 4:
         walk_column<4, COLOUR, COUNTS, false, LT0>(A, ks, tab, x0, i0,
                                                    (int)rows, lh, &ne);
@@ -137,18 +149,27 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_BATCH_MINB)
   }
 }
 
-cudaError_t launch_batch_pass(const LaunchParams &P, bool lt0,
+template <int COLOUR>
+static void launch_batch_colour(const LaunchParams &P, int kind,
+                                const StepDesc *d_step, int32_t s,
+                                size_t smem, cudaStream_t st) {
+  const dim3 grid((unsigned)P.ntiles), block(kPassThreads);
+  if (kind == kKindHB)
+    batch_pass_kernel<COLOUR, kKindHB><<<grid, block, smem, st>>>(P, d_step, s);
+  else if (kind == kKindLT0)
+    batch_pass_kernel<COLOUR, kKindLT0><<<grid, block, smem, st>>>(P, d_step, s);
+  else
+    batch_pass_kernel<COLOUR, kKindLE><<<grid, block, smem, st>>>(P, d_step, s);
+}
+
+cudaError_t launch_batch_pass(const LaunchParams &P, int kind,
                               const StepDesc *d_step, int32_t colour,
                               int32_t s, size_t smem, cudaStream_t st) {
   if (P.ntiles <= 0) return cudaSuccess;
-  const dim3 grid((unsigned)P.ntiles), block(kPassThreads);
-  if (colour) {
-    if (lt0) batch_pass_kernel<1, true><<<grid, block, smem, st>>>(P, d_step, s);
-    else batch_pass_kernel<1, false><<<grid, block, smem, st>>>(P, d_step, s);
-  } else {
-    if (lt0) batch_pass_kernel<0, true><<<grid, block, smem, st>>>(P, d_step, s);
-    else batch_pass_kernel<0, false><<<grid, block, smem, st>>>(P, d_step, s);
-  }
+  if (colour)
+    launch_batch_colour<1>(P, kind, d_step, s, smem, st);
+  else
+    launch_batch_colour<0>(P, kind, d_step, s, smem, st);
   return cudaGetLastError();
 }
 
@@ -322,16 +343,16 @@ int Engine::rebuild() {
     return qbits_for(members_[a]->q) < qbits_for(members_[b]->q);
   });
   for (int lane = 0; lane < lanes_; ++lane) {
-    for (int rule = 0; rule < 2; ++rule) {
+    for (int kind = 0; kind < 3; ++kind) {
       Unit u;
       for (size_t i : placed) {
-        if (member_lt0_[i] != rule || lane_of[i] != lane) continue;
+        if (member_kind_[i] != kind || lane_of[i] != lane) continue;
         if (!u.P || u.P->n == kMaxMembersPerLaunch) {
           if (u.P) units_.push_back(u);
           u = Unit();
           u.P = new (std::nothrow) LaunchParams();
           if (!u.P) return fail(POTTS_ENOMEM, "host allocation failed");
-          u.lt0 = rule == 1;
+          u.kind = kind;
           u.lane = lane;
         }
         Member *m = members_[i];
@@ -379,7 +400,7 @@ int Engine::launch_all(Slot &sl, int32_t kmax) {
   for (int32_t s = 0; s < kmax; ++s)
     for (int c = 0; c < 2; ++c)
       for (const Unit &u : units_)
-        POTTS_CK(launch_batch_pass(*u.P, u.lt0, sl.d_step, c, s,
+        POTTS_CK(launch_batch_pass(*u.P, u.kind, sl.d_step, c, s,
                                    (size_t)u.maxq * 32 * sizeof(uint32_t),
                                    u.lane ? aux_[u.lane - 1] : st_));
   for (int l = 1; l < lanes_; ++l) {  // join
@@ -422,18 +443,34 @@ int Engine::launch(int32_t k) {
     if (rc) return rc;
   }
   const size_t n = members_.size();
-  // the acceptance rule picks the kernel: a change regroups the members
-  member_lt0_.resize(n);
-  std::vector<AcceptTable> tabs(n);
+  // the update rule (and for Metropolis the acceptance rule) picks the
+  // kernel variant: a change regroups the members
+  member_kind_.resize(n);
+  std::vector<std::array<uint32_t, 9>> tabs(n);
   for (size_t i = 0; i < n; ++i) {
-    uint64_t thr[5];
-    if (!threshold_table(members_[i]->beta, thr))
-      return fail(POTTS_EINVAL, "beta must be finite and >= 0 (got %g)",
-                  members_[i]->beta);
-    tabs[i] = accept_table(thr);
-    const uint8_t lt0 = tabs[i].rule_lt0 ? 1 : 0;
-    if (lt0 != member_lt0_[i]) dirty_ = true;
-    member_lt0_[i] = lt0;
+    const Member *m = members_[i];
+    uint8_t kind;
+    if (m->update == POTTS_UPDATE_HEATBATH) {
+      uint64_t W[5];
+      int32_t e = 0;
+      if (!heatbath_table(m->beta, m->q, W, &e))
+        return fail(POTTS_EINVAL,
+                    "beta=%g is outside the heat-bath weights' range for q=%d",
+                    m->beta, m->q);
+      for (int j = 0; j < 8; ++j) tabs[i][j] = j < 5 ? (uint32_t)W[j] : 0u;
+      tabs[i][8] = (uint32_t)e;
+      kind = kKindHB;
+    } else {
+      uint64_t thr[5];
+      if (!threshold_table(m->beta, thr))
+        return fail(POTTS_EINVAL, "beta must be finite and >= 0 (got %g)",
+                    m->beta);
+      const AcceptTable T = accept_table(thr);
+      std::memcpy(tabs[i].data(), T.tab, sizeof T.tab);
+      kind = T.rule_lt0 ? kKindLT0 : kKindLE;
+    }
+    if (kind != member_kind_[i]) dirty_ = true;
+    member_kind_[i] = kind;
   }
   if (dirty_) {
     const int rc = rebuild();
@@ -456,7 +493,7 @@ int Engine::launch(int32_t k) {
     d.t0_lo = (uint32_t)m->sweep_next;
     d.t0_hi = (uint32_t)(m->sweep_next >> 32);
     d.nsweeps = std::max(0, std::min(m->nsweeps_step, k));
-    std::memcpy(d.tab, tabs[i].tab, sizeof d.tab);
+    std::memcpy(d.tab, tabs[i].data(), sizeof d.tab);
     d.rec = sl.d_rec + off;
     r.nsw[i] = d.nsweeps;
     r.off[i] = off;
@@ -746,6 +783,18 @@ int potts_batch_sweep(potts_batch_h b, const double *beta, int64_t nsweeps,
     }
     done += n;
   }
+  return POTTS_OK;
+}
+
+int potts_batch_set_update(potts_batch_h b, const int32_t *update) {
+  if (!b || !update) return fail(POTTS_EINVAL, "NULL argument");
+  for (size_t i = 0; i < b->members.size(); ++i)
+    if (update[i] != POTTS_UPDATE_METROPOLIS &&
+        update[i] != POTTS_UPDATE_HEATBATH)
+      return fail(POTTS_EINVAL, "lattice %zu: unknown update rule %d", i,
+                  update[i]);
+  for (size_t i = 0; i < b->members.size(); ++i)
+    b->members[i].update = update[i];
   return POTTS_OK;
 }
 

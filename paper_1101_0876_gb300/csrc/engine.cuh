@@ -42,13 +42,18 @@ struct StepDesc {
   uint32_t t0_lo, t0_hi;      // global index of the step's first sweep
   int32_t nsweeps;            // sweeps of this member in this step (<= k)
   uint32_t pad0;
-  uint32_t tab[9];            // acceptance table (see AcceptTable)
+  uint32_t tab[9];            // acceptance table (see AcceptTable), or for
+                              // heat bath W[0..7] (HeatTable) and m
   uint32_t pad1[3];
   unsigned long long *rec;    // [k][1 + q] records of this step
   unsigned long long pad2;
 };
 
 constexpr int kMaxMembersPerLaunch = 440;
+
+// Kernel variant of a member: Metropolis with acceptance rule LE or LT0
+// (see AcceptTable), or heat bath (StepDesc::tab then holds W[0..7] and m).
+enum { kKindLE = 0, kKindLT0 = 1, kKindHB = 2 };
 
 struct LaunchParams {
   int32_t n;        // members in this launch
@@ -68,6 +73,7 @@ struct Member {
   int64_t plane_bytes = 0;
   bool owns_planes = false;
   int32_t TR = 0;             // rows per walk (0: default)
+  int32_t update = POTTS_UPDATE_METROPOLIS;  // single-site rule
   int32_t nsweeps_step = 0;   // set by the caller before launch()
   potts_obs obs{};
   void *user = nullptr;       // owner's tag (serving loop)
@@ -130,7 +136,7 @@ class Engine {
  private:
   struct Unit {               // one launch: members sharing a rule
     LaunchParams *P = nullptr;
-    bool lt0 = false;
+    int kind = kKindLE;       // kKindLE, kKindLT0 (Metropolis) or kKindHB
     int32_t maxq = 2;
     int lane = 0;             // stream lane (0: st_, l > 0: aux_[l-1])
   };
@@ -161,7 +167,7 @@ class Engine {
   cudaMemPool_t pool_ = nullptr;
   int sm_count_ = 1;
   std::vector<Member *> members_;
-  std::vector<uint8_t> member_lt0_;
+  std::vector<uint8_t> member_kind_;
   bool dirty_ = true;
   uint64_t gen_ = 1;          // membership generation (graphs are per gen)
   uint64_t stable_ = 0;       // launches since the last rebuild
@@ -174,7 +180,7 @@ class Engine {
 };
 
 // One batched colour pass of the members of P at sweep offset s.
-cudaError_t launch_batch_pass(const LaunchParams &P, bool lt0,
+cudaError_t launch_batch_pass(const LaunchParams &P, int kind,
                               const StepDesc *d_step, int32_t colour,
                               int32_t s, size_t smem, cudaStream_t st);
 

@@ -169,6 +169,7 @@ struct potts_server {
         q->m.start = q->r.start;
         q->m.seed = q->r.seed;
         q->m.beta = q->r.beta;
+        q->m.update = q->r.update;
         q->m.user = q;
         q->to_launch = q->r.nsweeps;
         q->to_deliver = q->r.nsweeps;
@@ -317,6 +318,16 @@ int potts_serve_submit(potts_server_h s, const potts_req *req,
   uint64_t thr[5];
   if (!threshold_table(r.beta, thr))
     return fail(POTTS_EINVAL, "beta must be finite and >= 0");
+  if (r.update != POTTS_UPDATE_METROPOLIS && r.update != POTTS_UPDATE_HEATBATH)
+    return fail(POTTS_EINVAL, "unknown update rule %d", r.update);
+  if (r.update == POTTS_UPDATE_HEATBATH) {
+    uint64_t W[5];
+    int32_t e = 0;
+    if (!heatbath_table(r.beta, r.q, W, &e))
+      return fail(POTTS_EINVAL,
+                  "beta=%g is outside the heat-bath weights' range for q=%d",
+                  r.beta, r.q);
+  }
   if (potts_server::bytes_of(r) > s->cfg.hbm_budget_bytes)
     return fail(POTTS_EINVAL, "request needs %llu bytes, over the budget",
                 (unsigned long long)potts_server::bytes_of(r));

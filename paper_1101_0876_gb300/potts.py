@@ -47,7 +47,7 @@ class ServeCfg(ctypes.Structure):
 
 class Req(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("q", ctypes.c_int32),
-                ("start", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("start", ctypes.c_int32), ("update", ctypes.c_int32),
                 ("beta", ctypes.c_double), ("nsweeps", ctypes.c_int64),
                 ("seed", ctypes.c_uint64)]
 
@@ -78,6 +78,8 @@ _SIGS = {
     "potts_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double,
                                    ctypes.c_int64, _u64p]),
     "potts_set_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "potts_batch_set_update": (ctypes.c_int, [
+        ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
     "potts_heatbath_weights": (ctypes.c_int, [
         ctypes.c_double, ctypes.c_int32, _u64p,
         ctypes.POINTER(ctypes.c_int32)]),
@@ -326,6 +328,13 @@ class Batch:
                                       int(nsweeps), parr))
         return outs
 
+    def set_update(self, update) -> None:
+        """Per-lattice rule (UPDATE_METROPOLIS / UPDATE_HEATBATH) for
+        later sweeps."""
+        u = np.ascontiguousarray(update, dtype=np.int32)
+        assert u.size == self.n
+        check(lib().potts_batch_set_update(self._h, _ptr(u, ctypes.c_int32)))
+
     def spins(self, i: int) -> np.ndarray:
         out = np.empty((self.L[i], self.L[i]), dtype=np.uint8)
         check(lib().potts_batch_get_spins(self._h, int(i),
@@ -350,9 +359,10 @@ class Server:
         self._h = h
         self._q = {}
 
-    def submit(self, L, q, beta, nsweeps, seed, start=START_RANDOM) -> int:
-        r = Req(int(L), int(q), int(start), 0, float(beta), int(nsweeps),
-                int(seed))
+    def submit(self, L, q, beta, nsweeps, seed, start=START_RANDOM,
+               update=UPDATE_METROPOLIS) -> int:
+        r = Req(int(L), int(q), int(start), int(update), float(beta),
+                int(nsweeps), int(seed))
         rid = ctypes.c_uint64()
         check(lib().potts_serve_submit(self._h, ctypes.byref(r),
                                        ctypes.byref(rid)))

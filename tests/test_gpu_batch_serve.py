@@ -165,3 +165,41 @@ def test_serve_budget_queue_cancel_and_busy():
         srv.poll(12345)
     assert ei.value.code == potts.POTTS_ENOTFOUND
     srv.stop()
+
+
+# ------------------------------------------------------------- heat bath
+def test_batch_mixed_update_rules():
+    """Heat-bath and Metropolis lattices in one batch: each lattice's records
+    equal the oracle's with its own rule."""
+    L, q, st, sd, be = zip(*MIX)
+    rules = [potts.UPDATE_HEATBATH if i % 2 == 0 else potts.UPDATE_METROPOLIS
+             for i in range(len(MIX))]
+    be = [min(b, 5.0) for b in be]           # inside the heat-bath range
+    b = potts.Batch(L, q, st, sd)
+    b.set_update(rules)
+    recs = b.sweep(be, 23)
+    for i, (Li, qi, si, sdi, _) in enumerate(MIX):
+        o = oracle.Lattice(Li, qi, si, sdi)
+        ro = o.sweep(be[i], 23, update=rules[i])
+        assert np.array_equal(recs[i], ro), i
+        assert np.array_equal(b.spins(i), o.spins()), i
+    with pytest.raises(potts.PottsError):
+        b.set_update([5] * len(MIX))
+    b.close()
+
+
+def test_serve_heatbath_requests_alone_equal_mixed():
+    srv = potts.Server(hbm_budget_bytes=1 << 30, max_slots=3,
+                       sweeps_per_step=8)
+    reqs = [(64, 9, math.log(4.0), 30, 21, 1), (128, 15, 1.2, 20, 22, 0),
+            (96, 24, 1.0, 17, 23, 1), (160, 96, 2.0, 9, 24, 1),
+            (224, 9, 1.3, 25, 25, 0)]
+    rids = [srv.submit(L, q, b, n, s, update=u) for (L, q, b, n, s, u) in reqs]
+    got = _drain(srv, rids)
+    with pytest.raises(potts.PottsError) as ei:     # beyond the weights
+        srv.submit(64, 9, 7.0, 5, 1, update=potts.UPDATE_HEATBATH)
+    assert ei.value.code == potts.POTTS_EINVAL
+    srv.stop()
+    for rid, (L, q, b, n, s, u) in zip(rids, reqs):
+        o = oracle.Lattice(L, q, 1, s)
+        assert np.array_equal(got[rid], o.sweep(b, n, update=u)), rid
