@@ -172,6 +172,12 @@ def test_paper_scale_sampled(q, t_over_tc):
     _sampled_sweep_parity(cfg.L, q, cfg.start, cfg.seed, t_over_tc, warm=3)
 
 
+def test_maximum_size_L65536_sampled():
+    """The largest lattice the library accepts (L = 65536: 4.3e9 sites, two
+    2 GiB planes; site indices up to 2^31, Philox counters up to 2^30)."""
+    _sampled_sweep_parity(65536, 9, 1, 5, 1.0, warm=0, nsample=100_000)
+
+
 def test_q96_L16384_sampled():
     cfg = workloads.PAPER_Q96
     _sampled_sweep_parity(cfg.L, cfg.q, cfg.start, cfg.seed, 1.005, warm=2)
