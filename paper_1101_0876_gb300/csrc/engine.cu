@@ -589,7 +589,7 @@ int Engine::autotune(int32_t max_k) {
   std::vector<uint8_t *> saved(members_.size(), nullptr);
   std::vector<uint64_t> sweeps(members_.size());
   std::vector<potts_obs> obs(members_.size());
-  std::vector<int32_t> nst(members_.size()), trs(members_.size());
+  std::vector<int32_t> nst(members_.size());
   size_t total = 0;
   for (Member *m : members_) total += (size_t)(2 * m->plane_bytes);
   uint8_t *scratch = nullptr;
@@ -607,9 +607,7 @@ int Engine::autotune(int32_t max_k) {
                              cudaMemcpyDeviceToDevice, st_));
     sweeps[i] = m->sweep;
     obs[i] = m->obs;
-    (void)0;
     nst[i] = m->nsweeps_step;
-    trs[i] = m->TR;
   }
   cudaEvent_t e0, e1;
   POTTS_CK(cudaEventCreate(&e0));
@@ -662,7 +660,6 @@ int Engine::autotune(int32_t max_k) {
   tuned_tr_ = best_tr;
   tuned_k_ = best_k;
   dirty_ = true;
-  (void)trs;
   return rc;
 }
 
