@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(kPassThreads,
   for (uint32_t v = tid; v < q * 32u; v += kPassThreads) s_hist[v] = 0;
   if (tid == 0) s_sat = 0;
   __syncthreads();
+  pdl_wait_previous();
 
   PassArgs A;
   A.own = d.plane[COLOUR];
@@ -131,6 +132,7 @@ __global__ void __launch_bounds__(kPassThreads,
         break;
     }
   }
+  pdl_release_next();
   unsigned long long *rec = sd.rec + (int64_t)s * (1 + d.q);
   if (COUNTS) {
     uint32_t sat = 64u * rows - ne;
@@ -150,27 +152,26 @@ __global__ void __launch_bounds__(kPassThreads,
 }
 
 template <int COLOUR>
-static void launch_batch_colour(const LaunchParams &P, int kind,
+static cudaError_t launch_batch_colour(const LaunchParams &P, int kind,
                                 const StepDesc *d_step, int32_t s,
                                 size_t smem, cudaStream_t st) {
   const dim3 grid((unsigned)P.ntiles), block(kPassThreads);
   if (kind == kKindHB)
-    batch_pass_kernel<COLOUR, kKindHB><<<grid, block, smem, st>>>(P, d_step, s);
-  else if (kind == kKindLT0)
-    batch_pass_kernel<COLOUR, kKindLT0><<<grid, block, smem, st>>>(P, d_step, s);
-  else
-    batch_pass_kernel<COLOUR, kKindLE><<<grid, block, smem, st>>>(P, d_step, s);
+    return launch_pdl(batch_pass_kernel<COLOUR, kKindHB>, grid, block, smem,
+                      st, P, d_step, s);
+  if (kind == kKindLT0)
+    return launch_pdl(batch_pass_kernel<COLOUR, kKindLT0>, grid, block, smem,
+                      st, P, d_step, s);
+  return launch_pdl(batch_pass_kernel<COLOUR, kKindLE>, grid, block, smem, st,
+                    P, d_step, s);
 }
 
 cudaError_t launch_batch_pass(const LaunchParams &P, int kind,
                               const StepDesc *d_step, int32_t colour,
                               int32_t s, size_t smem, cudaStream_t st) {
   if (P.ntiles <= 0) return cudaSuccess;
-  if (colour)
-    launch_batch_colour<1>(P, kind, d_step, s, smem, st);
-  else
-    launch_batch_colour<0>(P, kind, d_step, s, smem, st);
-  return cudaGetLastError();
+  return colour ? launch_batch_colour<1>(P, kind, d_step, s, smem, st)
+                : launch_batch_colour<0>(P, kind, d_step, s, smem, st);
 }
 
 // ------------------------------------------------------------- engine

@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_HB_MINB)
     if (tid == 0) s_sat = 0;
   }
   __syncthreads();
+  pdl_wait_previous();
 
   const PhiloxKey ks = philox_schedule(A.key0, A.key1);
   const int32_t cx = (int32_t)tid % G.CX, rg = (int32_t)tid / G.CX;
@@ -56,6 +57,7 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_HB_MINB)
       rows_done += (uint32_t)rows;
     }
   }
+  pdl_release_next();
   if (!hist) return;
   if (COUNTS) {
     uint32_t sat = 64u * rows_done - ne;
@@ -96,8 +98,8 @@ cudaError_t launch_hb_c(const PassArgs &A, const HeatTable &T,
   const size_t smem =
       rec ? (size_t)(PAIRS ? kHbPairBins : A.hist_bins) * 32u * sizeof(uint32_t)
           : 0;
-  hb_pass_kernel<COLOUR, PAIRS, LAY><<<grid, block, smem, st>>>(A, T, G, rec);
-  return cudaGetLastError();
+  return launch_pdl(hb_pass_kernel<COLOUR, PAIRS, LAY>, grid, block, smem, st,
+                    A, T, G, rec);
 }
 
 template <int LAY>

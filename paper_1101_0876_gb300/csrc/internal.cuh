@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <string>
+#include <utility>
 
 #include "../../include/potts.h"
 #include "pass_u8.cuh"
@@ -44,6 +45,38 @@ constexpr int kPassThreads = 128;
 
 TileGeom choose_geom(int32_t L, int32_t H, int32_t q, int32_t sm_count,
                      int32_t tr_hint);
+
+// Programmatic dependent launch.  A colour pass is launched so that it may
+// start while the previous kernel on its stream finishes: its CTAs clear
+// their shared counters and load their tables, then wait for the previous
+// kernel to complete (and its writes to be visible) before touching the
+// lattice; each pass lets the next one start once its own walks are done,
+// so the next pass's launch and set-up overlap this pass's reduction tail.
+// Both calls are no-ops when a kernel was launched without the attribute.
+__device__ __forceinline__ void pdl_wait_previous() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_release_next() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launches kernel<<<grid, block, smem, st>>>(args...) with the programmatic
+// stream serialization attribute.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                       size_t smem, cudaStream_t st, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Spin-width class: every spin < 2^qbits.
 int qbits_for(int32_t q);
