@@ -14,8 +14,8 @@
 
 Every quantity is formed in FP64 from the exact per-sweep integer records
 {B, hist} (e = -B/N, m = (q N_max/N - 1)/(q - 1)).  `batch_factory` builds
-the batch (default: the CUDA batch of potts.Batch); the tests pass a CPU
-stand-in with the same interface to check the bookkeeping.
+the batch (default: potts.Batch, or potts.Lattice for a single sample); the
+tests pass a CPU stand-in with the same interface to check the bookkeeping.
 
 Command line:
     python -m paper_1101_0876_gb300.protocol x9          # Sec. 5 end-to-end run
@@ -38,8 +38,26 @@ from .analysis import energy_magnetization, exact_energies
 START_ORDERED, START_RANDOM = 0, 1
 
 
+class _OneLattice:
+    """A single lattice behind the batch interface: one sample runs on the
+    single-lattice path, whose direct launches beat a one-member batch."""
+
+    def __init__(self, L, q, start, seed):
+        from . import potts
+        self._lat = potts.Lattice(L[0], q[0], start[0], seed[0])
+
+    def sweep(self, beta, n, records=True):
+        out = self._lat.sweep(beta[0], n, records=records)
+        return [out] if records else None
+
+    def close(self):
+        self._lat.close()
+
+
 def _default_factory(L, q, start, seed):
     from . import potts
+    if len(L) == 1:
+        return _OneLattice(L, q, start, seed)
     return potts.Batch(L, q, start, seed)
 
 
