@@ -672,6 +672,7 @@ struct potts_batch {
   Engine eng;
   std::vector<Member> members;
   cudaStream_t stream = nullptr;
+  int device = 0;
   bool tuned = false;
   ~potts_batch() {
     for (Member &m : members) eng.free_member(&m);
@@ -704,7 +705,9 @@ int potts_batch_create(int32_t n, const int32_t *L, const int32_t *q,
   }
   potts_batch *b = new (std::nothrow) potts_batch();
   if (!b) return fail(POTTS_ENOMEM, "host allocation failed");
-  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess)
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     delete b;
     return fail(POTTS_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
@@ -738,6 +741,7 @@ int potts_batch_create(int32_t n, const int32_t *L, const int32_t *q,
 int potts_batch_sweep(potts_batch_h b, const double *beta, int64_t nsweeps,
                       uint64_t *const *out_counts) {
   if (!b || !beta) return fail(POTTS_EINVAL, "NULL argument");
+  DeviceScope device_scope(b->device);
   if (nsweeps < 0) return fail(POTTS_EINVAL, "nsweeps < 0");
   for (size_t i = 0; i < b->members.size(); ++i) {
     uint64_t thr[5];
@@ -798,6 +802,7 @@ int potts_batch_set_update(potts_batch_h b, const int32_t *update) {
 
 int potts_batch_get_spins(potts_batch_h b, int32_t i, uint8_t *out_LxL) {
   if (!b || !out_LxL) return fail(POTTS_EINVAL, "NULL argument");
+  DeviceScope device_scope(b->device);
   if (i < 0 || (size_t)i >= b->members.size())
     return fail(POTTS_EINVAL, "lattice index %d out of range", i);
   return b->eng.copy_spins(&b->members[(size_t)i], out_LxL);
@@ -814,6 +819,7 @@ int potts_batch_observables(potts_batch_h b, int32_t i, potts_obs *out) {
 
 int potts_batch_destroy(potts_batch_h b) {
   if (!b) return fail(POTTS_EINVAL, "handle is NULL");
+  DeviceScope device_scope(b->device);
   if (b->stream) cudaStreamSynchronize(b->stream);
   delete b;
   return POTTS_OK;

@@ -24,6 +24,27 @@ void clear_error();
                            cudaGetErrorString(e_), __FILE__, __LINE__);    \
   } while (0)
 
+// Makes a handle's device current for the scope of an entry point and
+// restores the caller's device afterwards (a process may hold handles on
+// several devices).
+class DeviceScope {
+ public:
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev_) == cudaSuccess && prev_ != dev &&
+        cudaSetDevice(dev) == cudaSuccess)
+      return;
+    prev_ = -1;
+  }
+  ~DeviceScope() {
+    if (prev_ >= 0) cudaSetDevice(prev_);
+  }
+  DeviceScope(const DeviceScope &) = delete;
+  DeviceScope &operator=(const DeviceScope &) = delete;
+
+ private:
+  int prev_ = -1;
+};
+
 // ---------------------------------------------------------- geometry
 // CTA work shape of a colour pass.  A row tile is CX 16-byte chunks wide
 // and RG row groups of TR rows high (128 threads: thread t takes chunk t%CX

@@ -263,6 +263,7 @@ int potts_create(int32_t L, int32_t q, int32_t start, uint64_t seed,
 
 int potts_sweep(potts_h h, double beta, int64_t nsweeps, uint64_t *out_counts) {
   if (!h) return fail(POTTS_EINVAL, "handle is NULL");
+  DeviceScope device_scope(h->device);
   if (nsweeps < 0) return fail(POTTS_EINVAL, "nsweeps < 0");
   uint64_t thr[5];
   if (!threshold_table(beta, thr))
@@ -351,6 +352,7 @@ int potts_reset_averages(potts_h h) {
 
 int potts_get_spins(potts_h h, uint8_t *out_LxL) {
   if (!h || !out_LxL) return fail(POTTS_EINVAL, "NULL argument");
+  DeviceScope device_scope(h->device);
   std::vector<uint8_t> tmp;
   try {
     tmp.resize((size_t)(2 * h->plane_bytes));
@@ -379,6 +381,7 @@ int potts_get_spins(potts_h h, uint8_t *out_LxL) {
 
 int potts_set_state(potts_h h, const uint8_t *LxL, uint64_t sweep) {
   if (!h || !LxL) return fail(POTTS_EINVAL, "NULL argument");
+  DeviceScope device_scope(h->device);
   const int64_t n = (int64_t)h->L * h->L;
   for (int64_t k = 0; k < n; ++k)
     if (LxL[k] >= h->q)
@@ -433,6 +436,7 @@ int potts_device_planes(potts_h h, void **white, void **black,
 
 int potts_destroy(potts_h h) {
   if (!h) return fail(POTTS_EINVAL, "handle is NULL");
+  DeviceScope device_scope(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   free_lattice(h);
   return POTTS_OK;
