@@ -487,7 +487,7 @@ def measure_served(args, single_updates_per_s):
     continuous-batching server with a 120 GB budget; latency = time the
     last record was polled - arrival time."""
     from paper_1101_0876_gb300 import potts, workloads
-    reqs = workloads.served(n=args.served_requests)
+    reqs = workloads.served(n=args.served_requests, rate_hz=args.served_rate)
     srv = potts.Server(hbm_budget_bytes=120 * 10**9,
                        max_slots=args.served_slots,
                        sweeps_per_step=args.served_k)
@@ -518,15 +518,19 @@ def measure_served(args, single_updates_per_s):
     def pct(p):
         return lat_ms[min(len(lat_ms) - 1, int(round(p / 100 * (len(lat_ms) - 1))))]
     busy = wall - reqs[0].arrival_s
+    offered = upd / max(reqs[-1].arrival_s, 1e-9)
     return {"requests": len(reqs), "updates": upd,
             "seconds": busy, "updates_per_s": upd / busy,
             "ratio_to_single": (upd / busy) / single_updates_per_s,
             "p50_ms": pct(50), "p99_ms": pct(99), "max_ms": lat_ms[-1],
-            "offered_updates_per_s": upd / max(reqs[-1].arrival_s, 1e-9),
+            "offered_updates_per_s": offered,
             "slots": args.served_slots, "sweeps_per_step": args.served_k,
+            "rate_hz": args.served_rate,
             "steps": st["steps"],
-            "note": "offered load exceeds capacity: latency grows with the "
-                    "backlog (saturated server)"}
+            "note": ("offered load exceeds capacity: latency grows with the "
+                     "backlog (saturated server)")
+            if offered > 0.9 * single_updates_per_s
+            else "offered load below the single-lattice rate"}
 
 
 # --------------------------------------------------- reference arm
@@ -608,6 +612,8 @@ def main():
     ap.add_argument("--batch-sweeps", type=int, default=500)
     ap.add_argument("--served-requests", type=int, default=200)
     ap.add_argument("--served-slots", type=int, default=64)
+    ap.add_argument("--served-rate", type=float, default=200.0,
+                    help="Poisson arrival rate of the served stream (req/s)")
     ap.add_argument("--served-k", type=int, default=32)
     ap.add_argument("--rng-ceiling", action="store_true",
                     help="time the random-number work alone and exit")
