@@ -21,6 +21,7 @@ Command line:
     python -m paper_1101_0876_gb300.protocol x9          # Sec. 5 end-to-end run
     python -m paper_1101_0876_gb300.protocol mid         # L=4096 heating+cooling
     python -m paper_1101_0876_gb300.protocol transition  # Table 2 at L=2048
+    python -m paper_1101_0876_gb300.protocol fig3        # Fig. 3 curves, L=2048
 Each prints one JSON line.
 """
 from __future__ import annotations
@@ -163,7 +164,9 @@ def _sem(x) -> float:
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("run", choices=["x9", "mid", "transition"])
+    ap.add_argument("run", choices=["x9", "mid", "transition", "fig3"])
+    ap.add_argument("--t-tran", type=int, default=10000)
+    ap.add_argument("--t-max", type=int, default=20000)
     ap.add_argument("--L", type=int, default=0)
     ap.add_argument("--samples", type=int, default=0)
     ap.add_argument("--t-eq", type=int, default=500000)
@@ -197,6 +200,25 @@ def main(argv=None):
                                 updates_per_s=heat[2] / heat[1]),
                    cooling=dict(rows=cool[0], seconds=cool[1],
                                 updates_per_s=cool[2] / cool[1]))
+    elif a.run == "fig3":
+        # Sec. 4, Fig. 3: e(T) and m(T) near T_c for q = 9, 12, 15, 96 on
+        # L = 2048, 10 samples, heating from the ordered start and cooling
+        # from the random start over T / T_c in [0.97, 1.03]
+        L, S = a.L or 2048, a.samples or 10
+        ratios = [0.97 + 0.005 * k for k in range(13)]
+        curves, secs_all, upd_all = {}, 0.0, 0
+        for q in (9, 12, 15, 96):
+            temps = [workloads.tc(q) * r for r in ratios]
+            heat = ladder(L, q, temps, a.t_tran, a.t_max, S, START_ORDERED,
+                          1000 * q)
+            cool = ladder(L, q, temps[::-1], a.t_tran, a.t_max, S,
+                          START_RANDOM, 1000 * q + 500)
+            curves[str(q)] = dict(heating=heat[0], cooling=cool[0][::-1])
+            secs_all += heat[1] + cool[1]
+            upd_all += heat[2] + cool[2]
+        out.update(L=L, samples=S, t_tran=a.t_tran, t_max=a.t_max,
+                   t_over_tc=ratios, curves=curves, seconds=secs_all,
+                   updates_per_s=upd_all / secs_all)
     else:
         L, S = a.L or 2048, a.samples or 10
         table, secs, upd = transition(a.q, L, S, a.t_eq, a.t_meas)
