@@ -14,7 +14,8 @@
  *     uniformly among the q states and accepted with probability
  *     min(1, exp(-beta dE)) (Sec. 2.2, Sec. 3.2).  One sweep (one MCS) is a
  *     pass over all white sites ((i+j) even) followed by a pass over all
- *     black sites (Sec. 3, "Red-Black Gauss-Seidel").
+ *     black sites (Sec. 3, "Red-Black Gauss-Seidel").  A heat-bath rule
+ *     (potts_set_update) is the alternative single-flip update.
  *   - Random numbers: counter-based Philox4x32-10 (Salmon et al., SC'11),
  *     keyed by (seed, sweep, colour, site), replacing the paper's per-thread
  *     multiply-with-carry generators (Sec. 3.2).  The word of colour-c site
@@ -43,7 +44,11 @@
  *   - Streams: each handle runs on its own CUDA stream unless
  *     potts_set_stream() gave it one; calls that return results to host
  *     memory synchronise that stream before returning.
- *   - Device: handles are bound to the device current at creation.
+ *   - Device: handles are bound to the device current at creation; calls
+ *     on a handle run on that device and restore the caller's current
+ *     device before returning.
+ *   - Version 200 (0.2.0) added the heat-bath rule (potts_set_update,
+ *     potts_heatbath_weights, potts_batch_set_update, potts_req.update).
  */
 #ifndef POTTS_H
 #define POTTS_H

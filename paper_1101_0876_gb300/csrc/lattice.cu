@@ -180,7 +180,7 @@ extern "C" {
 
 const char *potts_last_error(void) { return g_err.c_str(); }
 
-int potts_version(void) { return 100; }
+int potts_version(void) { return 200; }
 
 int potts_threshold_table(double beta, uint64_t out_thr[5]) {
   if (!out_thr) return fail(POTTS_EINVAL, "out_thr is NULL");
