@@ -89,6 +89,26 @@ def traffic_per_launch(L: int):
     return float(mb.group(1)) * (L * L) / (Lc * Lc)
 
 
+FULLSET_FILE = os.path.join(ROOT, "profiles", "colour_pass_L16384_q9.md")
+
+
+def instructions_per_site():
+    """Thread instructions per updated site of the white and black passes
+    from the committed full-set ncu summary (the ALU check beside the HBM
+    roofline); None when the kernel sources changed since the capture."""
+    try:
+        text = open(FULLSET_FILE).read()
+    except OSError:
+        return None
+    mh = re.search(r"Kernel sources hash:\s*([0-9a-f]+)", text)
+    mi = re.search(r"warp instructions \|[^|]*\(([0-9.]+) per updated site\) \|"
+                   r"[^|]*\(([0-9.]+) per site\)", text)
+    if not (mh and mi) or mh.group(1) != kernel_hash():
+        return None
+    return {"white": float(mi.group(1)), "black": float(mi.group(2)),
+            "source": "profiles/colour_pass_L16384_q9.md (ncu, L = 16384)"}
+
+
 # ------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
@@ -366,7 +386,8 @@ def run_ours(args):
                      "traffic": traffic_per_launch(L),
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "kernel": "colour pass (white; black fused with counts)",
-                     "bytes_per_launch": bytes_per_launch},
+                     "bytes_per_launch": bytes_per_launch,
+                     "inst_per_site": instructions_per_site()},
         "clocks": clocks.summary(),
     }
     if ws == 1 and not args.no_u4:
