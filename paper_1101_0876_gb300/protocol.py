@@ -47,6 +47,9 @@ class _OneLattice:
         from . import potts
         self._lat = potts.Lattice(L[0], q[0], start[0], seed[0])
 
+    def set_update(self, update):
+        self._lat.set_update(int(update[0]))
+
     def sweep(self, beta, n, records=True):
         out = self._lat.sweep(beta[0], n, records=records)
         return [out] if records else None
@@ -63,7 +66,8 @@ def _default_factory(L, q, start, seed):
 
 
 def ladder(L: int, q: int, temps, t_tran: int, t_max: int, samples: int,
-           start: int, seed0: int = 1, batch_factory=None, chunk: int = 4000):
+           start: int, seed0: int = 1, batch_factory=None, chunk: int = 4000,
+           update: int = 0):
     """Runs `samples` independent lattices (seeds seed0 + s) through the
     temperature sequence `temps` (absolute T, visited in the given order).
     Returns (rows, seconds, updates): rows[k] = dict(T, e, m, e_err, m_err)
@@ -72,6 +76,8 @@ def ladder(L: int, q: int, temps, t_tran: int, t_max: int, samples: int,
     factory = batch_factory or _default_factory
     b = factory([L] * samples, [q] * samples, [start] * samples,
                 [seed0 + s for s in range(samples)])
+    if update:
+        b.set_update([update] * samples)
     rows = []
     t0 = time.perf_counter()
     for T in temps:
@@ -99,7 +105,8 @@ def ladder(L: int, q: int, temps, t_tran: int, t_max: int, samples: int,
 
 
 def transition(qs, L: int, samples: int, t_eq: int, t_meas: int,
-               seed0: int = 100, batch_factory=None, chunk: int = 2000):
+               seed0: int = 100, batch_factory=None, chunk: int = 2000,
+               update: int = 0):
     """Both branches at exactly T_c for every q in qs, all in one batch:
     per q, `samples` lattices started ordered and `samples` started at
     random (seeds seed0 + 1000 q + s and seed0 + 1000 q + 500 + s).
@@ -117,6 +124,8 @@ def transition(qs, L: int, samples: int, t_eq: int, t_meas: int,
                 beta.append(workloads.beta_at(q, 1.0))
     n = len(Ls)
     b = factory(Ls, qq, st, sd)
+    if update:
+        b.set_update([update] * n)
     t0 = time.perf_counter()
     left = t_eq
     while left > 0:
@@ -172,16 +181,21 @@ def main(argv=None):
     ap.add_argument("--t-eq", type=int, default=500000)
     ap.add_argument("--t-meas", type=int, default=500000)
     ap.add_argument("--q", type=int, nargs="*", default=[6, 9, 15, 96])
+    ap.add_argument("--update", choices=["metropolis", "heatbath"],
+                    default="metropolis")
     a = ap.parse_args(argv)
-    out = {"run": a.run}
+    upd_rule = 1 if a.update == "heatbath" else 0
+    out = {"run": a.run, "update": a.update}
     if a.run == "x9":
         # Sec. 5 end-to-end run: q=9, L=1024, 3 samples, T from 0.71 to
         # 0.73 in steps of 0.002, t_tran = 2000, t_max = 8000 (records every
         # sweep, a superset of the paper's delta t = 50); both directions.
         L, q, S = a.L or 1024, 9, a.samples or 3
         temps = [0.71 + 0.002 * k for k in range(11)]
-        heat = ladder(L, q, temps, 2000, 8000, S, START_ORDERED, 1)
-        cool = ladder(L, q, temps[::-1], 2000, 8000, S, START_RANDOM, 101)
+        heat = ladder(L, q, temps, 2000, 8000, S, START_ORDERED, 1,
+                      update=upd_rule)
+        cool = ladder(L, q, temps[::-1], 2000, 8000, S, START_RANDOM, 101,
+                      update=upd_rule)
         out.update(L=L, q=q, samples=S,
                    heating=dict(rows=heat[0], seconds=heat[1],
                                 updates_per_s=heat[2] / heat[1]),
@@ -193,8 +207,10 @@ def main(argv=None):
         L, q = a.L or cfg["L"], cfg["q"]
         temps = [workloads.tc(q) * t for t in cfg["ladder"]]
         n = cfg["sweeps_per_t"]
-        heat = ladder(L, q, temps, 0, n, 1, START_ORDERED, cfg["seed"])
-        cool = ladder(L, q, temps[::-1], 0, n, 1, START_RANDOM, cfg["seed"])
+        heat = ladder(L, q, temps, 0, n, 1, START_ORDERED, cfg["seed"],
+                      update=upd_rule)
+        cool = ladder(L, q, temps[::-1], 0, n, 1, START_RANDOM, cfg["seed"],
+                      update=upd_rule)
         out.update(L=L, q=q,
                    heating=dict(rows=heat[0], seconds=heat[1],
                                 updates_per_s=heat[2] / heat[1]),
@@ -210,9 +226,9 @@ def main(argv=None):
         for q in (9, 12, 15, 96):
             temps = [workloads.tc(q) * r for r in ratios]
             heat = ladder(L, q, temps, a.t_tran, a.t_max, S, START_ORDERED,
-                          1000 * q)
+                          1000 * q, update=upd_rule)
             cool = ladder(L, q, temps[::-1], a.t_tran, a.t_max, S,
-                          START_RANDOM, 1000 * q + 500)
+                          START_RANDOM, 1000 * q + 500, update=upd_rule)
             curves[str(q)] = dict(heating=heat[0], cooling=cool[0][::-1])
             secs_all += heat[1] + cool[1]
             upd_all += heat[2] + cool[2]
@@ -221,7 +237,8 @@ def main(argv=None):
                    updates_per_s=upd_all / secs_all)
     else:
         L, S = a.L or 2048, a.samples or 10
-        table, secs, upd = transition(a.q, L, S, a.t_eq, a.t_meas)
+        table, secs, upd = transition(a.q, L, S, a.t_eq, a.t_meas,
+                                      update=upd_rule)
         out.update(L=L, samples=S, t_eq=a.t_eq, t_meas=a.t_meas,
                    seconds=secs, updates_per_s=upd / secs,
                    table={str(k): v for k, v in table.items()})

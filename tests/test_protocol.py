@@ -16,8 +16,13 @@ class OracleBatch:
                     zip(L, q, start, seed)]
         self.closed = False
 
+    def set_update(self, update):
+        self.update = list(update)
+
     def sweep(self, beta, n, records=True):
-        out = [x.sweep(b, n, records=records) for x, b in zip(self.lat, beta)]
+        upd = getattr(self, "update", [0] * len(self.lat))
+        out = [x.sweep(b, n, records=records, update=u)
+               for x, b, u in zip(self.lat, beta, upd)]
         return out if records else None
 
     def close(self):
@@ -72,3 +77,16 @@ def test_transition_groups_branches_per_q():
         assert np.isclose(t["e_o"], br[0][0], rtol=0, atol=1e-12)
         assert np.isclose(t["e_d"], br[1][0], rtol=0, atol=1e-12)
         assert np.isclose(t["dm"], br[0][1] - br[1][1], rtol=0, atol=1e-12)
+
+
+def test_heatbath_rule_reaches_every_lattice():
+    L, q, S = 8, 3, 2
+    rows, _, _ = protocol.ladder(L, q, [1.1], 3, 5, S, protocol.START_RANDOM,
+                                 seed0=9, batch_factory=OracleBatch,
+                                 update=oracle.HEATBATH)
+    es = []
+    for s in range(S):
+        h = oracle.Lattice(L, q, 1, 9 + s)
+        h.sweep(1.0 / 1.1, 3, records=False, update=oracle.HEATBATH)
+        es.append(_means(h.sweep(1.0 / 1.1, 5, update=oracle.HEATBATH), L, q)[0])
+    assert np.isclose(rows[0]["e"], np.mean(es), rtol=0, atol=1e-12)
