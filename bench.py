@@ -511,7 +511,10 @@ def measure_served(args, single_updates_per_s):
     reqs = workloads.served(n=args.served_requests, rate_hz=args.served_rate)
     srv = potts.Server(hbm_budget_bytes=120 * 10**9,
                        max_slots=args.served_slots,
-                       sweeps_per_step=args.served_k)
+                       sweeps_per_step=args.served_k,
+                       policy=(potts.ADMIT_SMALLEST
+                               if args.served_policy == "smallest"
+                               else potts.ADMIT_FIFO))
     import numpy as np
     buf = np.empty(8192 * 257, dtype=np.uint64)   # reused by every poll
     t0 = time.perf_counter()
@@ -546,7 +549,7 @@ def measure_served(args, single_updates_per_s):
             "p50_ms": pct(50), "p99_ms": pct(99), "max_ms": lat_ms[-1],
             "offered_updates_per_s": offered,
             "slots": args.served_slots, "sweeps_per_step": args.served_k,
-            "rate_hz": args.served_rate,
+            "rate_hz": args.served_rate, "policy": args.served_policy,
             "steps": st["steps"],
             "note": ("offered load exceeds capacity: latency grows with the "
                      "backlog (saturated server)")
@@ -633,6 +636,8 @@ def main():
     ap.add_argument("--batch-sweeps", type=int, default=500)
     ap.add_argument("--served-requests", type=int, default=200)
     ap.add_argument("--served-slots", type=int, default=64)
+    ap.add_argument("--served-policy", choices=["fifo", "smallest"],
+                    default="fifo", help="admission order of the server")
     ap.add_argument("--served-rate", type=float, default=200.0,
                     help="Poisson arrival rate of the served stream (req/s)")
     ap.add_argument("--served-k", type=int, default=32)

@@ -243,8 +243,16 @@ typedef struct {
   int32_t max_slots;          /* lattices active at once */
   int32_t sweeps_per_step;    /* sweeps per batched step (>= 1) */
   int32_t queue_capacity;     /* pending requests before EBUSY (0 = 65536) */
-  int32_t reserved;
+  int32_t policy;             /* admission order: POTTS_ADMIT_FIFO (0) or
+                                 POTTS_ADMIT_SMALLEST (1) */
 } potts_serve_cfg;
+
+/* Admission order of queued requests.  FIFO: oldest first; a request that
+ * does not fit the free budget blocks the ones behind it.  SMALLEST: the
+ * queued request with the least work (L^2 * nsweeps, ties: oldest) among
+ * those that fit is admitted next, which lowers the median latency under
+ * overload; a large request can wait while smaller ones keep arriving. */
+enum { POTTS_ADMIT_FIFO = 0, POTTS_ADMIT_SMALLEST = 1 };
 
 typedef struct {
   int32_t L, q, start;

@@ -1,7 +1,7 @@
 // Serving loop: continuous batching of simulation requests on one GPU.
 //
 // A host thread owns an Engine.  Each iteration it (1) admits queued
-// requests, oldest first, while a slot is free and the device bytes in use
+// requests (oldest first, or smallest work first), while a slot is free and the device bytes in use
 // plus the request's planes fit the budget, allocating and initialising
 // their lattices; (2) drops cancelled requests; (3) runs one batched step of
 // up to sweeps_per_step sweeps over every active lattice; (4) appends each
@@ -67,6 +67,10 @@ struct potts_server {
 
   static uint64_t bytes_of(const potts_req &r) {
     return (uint64_t)r.L * (uint64_t)r.L;
+  }
+  // spin updates a request asks for
+  static uint64_t work_of(const potts_req &r) {
+    return (uint64_t)r.L * (uint64_t)r.L * (uint64_t)r.nsweeps;
   }
 
   // Leaves the engine: slot and memory are free for the next admission
@@ -138,14 +142,26 @@ struct potts_server {
             ++it;
           }
         }
-        // admission: FIFO, by slot and by HBM budget
+        // admission by slot and by HBM budget, in the configured order
         while (!queue.empty() &&
                (int32_t)(active.size() + admit.size()) < cfg.max_slots) {
-          Request *q = queue.front();
-          const uint64_t b = bytes_of(q->r);
-          if (stats.bytes_in_use + b > cfg.hbm_budget_bytes) break;
-          queue.pop_front();
-          stats.bytes_in_use += b;
+          auto pick = queue.end();
+          if (cfg.policy == POTTS_ADMIT_SMALLEST) {
+            for (auto it = queue.begin(); it != queue.end(); ++it) {
+              if (stats.bytes_in_use + bytes_of((*it)->r) >
+                  cfg.hbm_budget_bytes)
+                continue;
+              if (pick == queue.end() || work_of((*it)->r) < work_of((*pick)->r))
+                pick = it;
+            }
+          } else if (stats.bytes_in_use + bytes_of(queue.front()->r) <=
+                     cfg.hbm_budget_bytes) {
+            pick = queue.begin();
+          }
+          if (pick == queue.end()) break;
+          Request *q = *pick;
+          queue.erase(pick);
+          stats.bytes_in_use += bytes_of(q->r);
           admit.push_back(q);
         }
         // cancellations of admitted requests
@@ -271,7 +287,8 @@ int potts_serve_start(const potts_serve_cfg *cfg, potts_server_h *out) {
   if (!cfg || !out) return fail(POTTS_EINVAL, "NULL argument");
   *out = nullptr;
   if (cfg->max_slots <= 0 || cfg->sweeps_per_step <= 0 ||
-      cfg->hbm_budget_bytes == 0 || cfg->queue_capacity < 0)
+      cfg->hbm_budget_bytes == 0 || cfg->queue_capacity < 0 ||
+      (cfg->policy != POTTS_ADMIT_FIFO && cfg->policy != POTTS_ADMIT_SMALLEST))
     return fail(POTTS_EINVAL, "max_slots, sweeps_per_step and the budget "
                               "must be positive");
   potts_server *s = new (std::nothrow) potts_server();

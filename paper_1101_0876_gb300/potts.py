@@ -17,6 +17,7 @@ POTTS_ETIMEOUT, POTTS_EBUSY, POTTS_ECANCELLED, POTTS_ENOTFOUND = 4, 5, 6, 7
 START_ORDERED, START_RANDOM = 0, 1
 LAYOUT_AUTO, LAYOUT_U8, LAYOUT_U4 = 0, 1, 2
 UPDATE_METROPOLIS, UPDATE_HEATBATH = 0, 1
+ADMIT_FIFO, ADMIT_SMALLEST = 0, 1
 
 _u8p = ctypes.POINTER(ctypes.c_uint8)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -42,7 +43,7 @@ class ServeCfg(ctypes.Structure):
                 ("max_slots", ctypes.c_int32),
                 ("sweeps_per_step", ctypes.c_int32),
                 ("queue_capacity", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("policy", ctypes.c_int32)]
 
 
 class Req(ctypes.Structure):
@@ -351,9 +352,10 @@ class Server:
     """Continuous-batching request loop running on a library host thread."""
 
     def __init__(self, hbm_budget_bytes: int, max_slots: int,
-                 sweeps_per_step: int, queue_capacity: int = 0):
+                 sweeps_per_step: int, queue_capacity: int = 0,
+                 policy: int = ADMIT_FIFO):
         cfg = ServeCfg(int(hbm_budget_bytes), int(max_slots),
-                       int(sweeps_per_step), int(queue_capacity), 0)
+                       int(sweeps_per_step), int(queue_capacity), int(policy))
         h = ctypes.c_void_p()
         check(lib().potts_serve_start(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

@@ -203,3 +203,37 @@ def test_serve_heatbath_requests_alone_equal_mixed():
     for rid, (L, q, b, n, s, u) in zip(rids, reqs):
         o = oracle.Lattice(L, q, 1, s)
         assert np.array_equal(got[rid], o.sweep(b, n, update=u)), rid
+
+
+@pytest.mark.parametrize("policy", [potts.ADMIT_FIFO, potts.ADMIT_SMALLEST])
+def test_serve_admission_policy(policy):
+    """One slot, held by a long request while a large and then a small
+    request queue up: FIFO runs the large one first, SMALLEST the small
+    one; both give the oracle's records."""
+    srv = potts.Server(hbm_budget_bytes=1 << 30, max_slots=1,
+                       sweeps_per_step=4, policy=policy)
+    a = srv.submit(256, 9, 1.0, 10**7, 1)
+    t0 = time.time()
+    while srv.stats()["active"] < 1 and time.time() - t0 < 30:
+        time.sleep(0.01)
+    big = srv.submit(512, 9, 1.0, 120, 2)
+    small = srv.submit(64, 9, 1.0, 20, 3)
+    srv.cancel(a)
+    order, got, pending = [], {big: [], small: []}, {big, small}
+    t0 = time.time()
+    while pending and time.time() - t0 < 60:
+        for r in list(pending):
+            rec, done = srv.poll(r)
+            if rec.size:
+                got[r].append(rec)
+            if done:
+                order.append(r)
+                pending.discard(r)
+        time.sleep(0.002)
+    srv.stop()
+    assert not pending
+    assert order == ([big, small] if policy == potts.ADMIT_FIFO
+                     else [small, big])
+    for r, (L, n, s) in ((big, (512, 120, 2)), (small, (64, 20, 3))):
+        ro, _ = _oracle_run(L, 9, 1, s, 1.0, n)
+        assert np.array_equal(np.concatenate(got[r]), ro), r
