@@ -114,8 +114,25 @@ __global__ void __launch_bounds__(kPassThreads,
     uint32_t *lh = s_hist + (tid & 31u);
     const int32_t x0 = chunk * 16;
     if (KIND == kKindHB) {
-      hb_walk_column<COLOUR, COUNTS, false, kLayoutU8>(
-          A, ks, s_tab, sd.tab[8], x0, i0, (int)rows, lh, &ne);
+      const uint32_t m = sd.tab[8];
+      switch (d.qbits) {
+        case 4:
+          hb_walk_column<4, COLOUR, COUNTS, false, kLayoutU8>(
+              A, ks, s_tab, m, x0, i0, (int)rows, lh, &ne);
+          break;
+        case 5:
+          hb_walk_column<5, COLOUR, COUNTS, false, kLayoutU8>(
+              A, ks, s_tab, m, x0, i0, (int)rows, lh, &ne);
+          break;
+        case 6:
+          hb_walk_column<6, COLOUR, COUNTS, false, kLayoutU8>(
+              A, ks, s_tab, m, x0, i0, (int)rows, lh, &ne);
+          break;
+        default:
+          hb_walk_column<8, COLOUR, COUNTS, false, kLayoutU8>(
+              A, ks, s_tab, m, x0, i0, (int)rows, lh, &ne);
+          break;
+      }
     } else switch (d.qbits) {
       case 4:
         walk_column<4, COLOUR, COUNTS, false, LT0>(A, ks, tab, x0, i0,

@@ -14,15 +14,15 @@ namespace {
 constexpr int kHbPairBins = 256;
 
 // Resident CTAs per SM asked of the compiler: the heat-bath rule keeps more
-// values live per site than the Metropolis one (at 3, up to 168 registers
-// and no spills).
+// values live than the Metropolis one; the word rule (QB <= 6) fits 128
+// registers (4 CTAs), the per-site rule (QB 8) 168 (3 CTAs), without spills.
 #ifndef POTTS_HB_MINB
 #define POTTS_HB_MINB 3
 #endif
 
 // Same grid, walk and reductions as the Metropolis pass kernel.
-template <int COLOUR, bool PAIRS, int LAY>
-__global__ void __launch_bounds__(kPassThreads, POTTS_HB_MINB)
+template <int QB, int COLOUR, bool PAIRS, int LAY>
+__global__ void __launch_bounds__(kPassThreads, QB <= 6 ? 4 : POTTS_HB_MINB)
     hb_pass_kernel(PassArgs A, HeatTable T, TileGeom G,
                    unsigned long long *rec) {
   constexpr bool COUNTS = COLOUR == 1;
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_HB_MINB)
       const int32_t i0 = (tile * G.RG + rg) * G.TR;
       if (i0 >= A.L) continue;
       const int32_t rows = min(G.TR, A.L - i0);
-      hb_walk_column<COLOUR, COUNTS, PAIRS, LAY>(
+      hb_walk_column<QB, COLOUR, COUNTS, PAIRS, LAY>(
           A, ks, s_W, T.m, chunk * 16, i0, rows,
           hist ? s_hist + (tid & 31u) : nullptr, &ne);
       rows_done += (uint32_t)rows;
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_HB_MINB)
   }
 }
 
-template <int COLOUR, bool PAIRS, int LAY>
+template <int QB, int COLOUR, bool PAIRS, int LAY>
 cudaError_t launch_hb_c(const PassArgs &A, const HeatTable &T,
                         const TileGeom &G, unsigned long long *rec,
                         cudaStream_t st) {
@@ -98,20 +98,21 @@ cudaError_t launch_hb_c(const PassArgs &A, const HeatTable &T,
   const size_t smem =
       rec ? (size_t)(PAIRS ? kHbPairBins : A.hist_bins) * 32u * sizeof(uint32_t)
           : 0;
-  return launch_pdl(hb_pass_kernel<COLOUR, PAIRS, LAY>, grid, block, smem, st,
-                    A, T, G, rec);
+  return launch_pdl(hb_pass_kernel<QB, COLOUR, PAIRS, LAY>, grid, block,
+                    smem, st, A, T, G, rec);
 }
 
-template <int LAY>
+template <int QB, int LAY>
 cudaError_t launch_hb_lay(const PassArgs &A, const HeatTable &T,
                           const TileGeom &G, unsigned long long *rec,
                           cudaStream_t st) {
-  const bool pairs = G.pairs && A.q <= 16;
-  if (pairs)
-    return A.colour ? launch_hb_c<1, true, LAY>(A, T, G, rec, st)
-                    : launch_hb_c<0, true, LAY>(A, T, G, rec, st);
-  return A.colour ? launch_hb_c<1, false, LAY>(A, T, G, rec, st)
-                  : launch_hb_c<0, false, LAY>(A, T, G, rec, st);
+  if constexpr (QB == 4) {
+    if (G.pairs)
+      return A.colour ? launch_hb_c<4, 1, true, LAY>(A, T, G, rec, st)
+                      : launch_hb_c<4, 0, true, LAY>(A, T, G, rec, st);
+  }
+  return A.colour ? launch_hb_c<QB, 1, false, LAY>(A, T, G, rec, st)
+                  : launch_hb_c<QB, 0, false, LAY>(A, T, G, rec, st);
 }
 
 // Largest normaliser over the ways four neighbours split into k distinct
@@ -169,9 +170,14 @@ cudaError_t launch_pass_hb(const PassArgs &A, const HeatTable &T,
                            cudaStream_t st) {
   if (A.layout == kLayoutU4) {
     if (A.q > 16) return cudaErrorInvalidValue;
-    return launch_hb_lay<kLayoutU4>(A, T, G, rec, st);
+    return launch_hb_lay<4, kLayoutU4>(A, T, G, rec, st);
   }
-  return launch_hb_lay<kLayoutU8>(A, T, G, rec, st);
+  switch (qbits_for((int32_t)A.q)) {
+    case 4: return launch_hb_lay<4, kLayoutU8>(A, T, G, rec, st);
+    case 5: return launch_hb_lay<5, kLayoutU8>(A, T, G, rec, st);
+    case 6: return launch_hb_lay<6, kLayoutU8>(A, T, G, rec, st);
+    default: return launch_hb_lay<8, kLayoutU8>(A, T, G, rec, st);
+  }
 }
 
 }  // namespace potts

@@ -78,8 +78,84 @@ __device__ __forceinline__ uint32_t hb_byte(uint32_t w, int b) {
   return __byte_perm(w, 0u, 0x4440u + (uint32_t)b);
 }
 
+// 1 per byte where a >= b, for bytes below 128.
+__device__ __forceinline__ uint32_t hb_ge(uint32_t a, uint32_t b) {
+  return (((a | 0x80808080u) - b) & 0x80808080u) >> 7;
+}
+
+// The four sites of one word at once (spins < 2^QB, QB <= 6): the same
+// rule as hb_site, with the neighbour comparisons, counts, first
+// appearances and weight indices done per byte on whole words, and the
+// unheld-state index moved past the held states by their ranks instead of
+// a sort (the idx-th unheld state is idx + #{held d : d - rank(d) <= idx}).
+// U, D, Lw, Rw: neighbour words (up, down, left, right); uw: Philox words.
+template <int QB>
+__device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
+                                            uint32_t Lw, uint32_t Rw,
+                                            const uint32_t uw[4], uint32_t q,
+                                            const uint32_t *sW, uint32_t m) {
+  static_assert(QB <= 6, "byte sums below need spins < 64");
+  constexpr uint32_t K = Swar<QB>::K, M = Swar<QB>::M;
+  constexpr uint32_t ONE = 0x01010101u, FIVE = 0x05050505u;
+  constexpr uint32_t SENT = 0x7F7F7F7Fu;  // above every state < 64
+  // 2^QB per byte where two neighbours are equal
+  const uint32_t E01 = ~((U ^ D) + K) & M, E02 = ~((U ^ Lw) + K) & M;
+  const uint32_t E03 = ~((U ^ Rw) + K) & M, E12 = ~((D ^ Lw) + K) & M;
+  const uint32_t E13 = ~((D ^ Rw) + K) & M, E23 = ~((Lw ^ Rw) + K) & M;
+  // first appearances (1 per byte) and their byte masks
+  const uint32_t F1 = (E01 ^ M) >> QB;
+  const uint32_t F2 = (~(E02 | E12) & M) >> QB;
+  const uint32_t F3 = (~(E03 | E13 | E23) & M) >> QB;
+  const uint32_t m1 = F1 * 0xFFu, m2 = F2 * 0xFFu, m3 = F3 * 0xFFu;
+  // weight indices: the class's neighbour count, 5 (weight 0) for repeats
+  const uint32_t I0 = ONE + ((E01 + E02 + E03) >> QB);
+  const uint32_t I1 = ((ONE + ((E12 + E13) >> QB)) & m1) | (FIVE & ~m1);
+  const uint32_t I2 = ((ONE + (E23 >> QB)) & m2) | (FIVE & ~m2);
+  const uint32_t I3 = (ONE & m3) | (FIVE & ~m3);
+  const uint32_t KC = ONE + F1 + F2 + F3;  // distinct neighbour states
+  // held states (repeats replaced by SENT), their ranks and thresholds
+  const uint32_t H1 = (D & m1) | (SENT & ~m1);
+  const uint32_t H2 = (Lw & m2) | (SENT & ~m2);
+  const uint32_t H3 = (Rw & m3) | (SENT & ~m3);
+  const uint32_t g01 = hb_ge(U, H1), g02 = hb_ge(U, H2), g03 = hb_ge(U, H3);
+  const uint32_t g12 = hb_ge(H1, H2), g13 = hb_ge(H1, H3), g23 = hb_ge(H2, H3);
+  const uint32_t T0 = U - (g01 + g02 + g03);
+  const uint32_t T1 = H1 - ((g01 ^ ONE) + g12 + g13);
+  const uint32_t T2 = H2 - ((g02 ^ ONE) + (g12 ^ ONE) + g23);
+  const uint32_t T3 = H3 - ((g03 ^ ONE) + (g13 ^ ONE) + (g23 ^ ONE));
+  const uint32_t qW0 = q << m;
+  uint32_t idx[4], cls[4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const uint32_t w0 = sW[hb_byte(I0, b)], w1 = sW[hb_byte(I1, b)];
+    const uint32_t w2 = sW[hb_byte(I2, b)], w3 = sW[hb_byte(I3, b)];
+    const uint32_t s1 = w0, s2 = s1 + w1, s3 = s2 + w2, s4 = s3 + w3;
+    const uint32_t Z = s4 + qW0 - (hb_byte(KC, b) << m);
+    const uint32_t r = __umulhi(uw[b], Z);
+    idx[b] = min((r - s4) >> m, 0x40u);  // < q - k <= 62 when used
+    cls[b] = (uint32_t)(r >= s1) + (uint32_t)(r >= s2) + (uint32_t)(r >= s3) +
+             (uint32_t)(r >= s4);
+  }
+  const uint32_t IDX = pack4(idx[0], idx[1], idx[2], idx[3]);
+  const uint32_t CLS = pack4(cls[0], cls[1], cls[2], cls[3]);
+  const uint32_t P =
+      IDX + hb_ge(IDX, T0) + hb_ge(IDX, T1) + hb_ge(IDX, T2) + hb_ge(IDX, T3);
+  // per byte: class 0..3 takes that neighbour, 4 the unheld state
+  auto is = [&](uint32_t c) {
+    const uint32_t x = CLS ^ (c * ONE);  // 0 where equal, bytes < 8
+    return ((((x + 0x7F7F7F7Fu) | x) & 0x80808080u) >> 7) * 0xFFu ^ 0xFFFFFFFFu;
+  };
+  uint32_t N = P;
+  N = (U & is(0u)) | (N & ~is(0u));
+  N = (D & is(1u)) | (N & ~is(1u));
+  N = (Lw & is(2u)) | (N & ~is(2u));
+  N = (Rw & is(3u)) | (N & ~is(3u));
+  return N;
+}
+
 // One row of 16 sites (the Metropolis do_row with the heat-bath rule).
-template <bool LEFT, bool COUNTS, bool PAIRS, int LAY>
+// QB <= 6: the word rule; QB 8: the per-site rule (any q <= 256).
+template <int QB, bool LEFT, bool COUNTS, bool PAIRS, int LAY>
 __device__ __forceinline__ void hb_row(const PassArgs &A, const PhiloxKey &ks,
                                        const uint32_t *sW, uint32_t m,
                                        Walk &w, int32_t x0, int32_t xb,
@@ -120,16 +196,20 @@ __device__ __forceinline__ void hb_row(const PassArgs &A, const PhiloxKey &ks,
     // side neighbour is at x-1, else x (Cw) and x+1 (Wd)
     const uint32_t Lw = LEFT ? Wd[k] : Cw[k];
     const uint32_t Rw = LEFT ? Cw[k] : Wd[k];
-    uint32_t s[4];
+    if constexpr (QB <= 6) {
+      Nw[k] = hb_word<QB>(w.Up[k], Dw[k], Lw, Rw, uw, A.q, sW, m);
+    } else {
+      uint32_t s[4];
 #pragma unroll
-    for (int b = 0; b < 4; ++b)
-      s[b] = hb_site(hb_byte(w.Up[k], b), hb_byte(Dw[k], b),
-                     hb_byte(Lw, b), hb_byte(Rw, b), uw[b], A.q, sW, m);
-    Nw[k] = pack4(s[0], s[1], s[2], s[3]);
+      for (int b = 0; b < 4; ++b)
+        s[b] = hb_site(hb_byte(w.Up[k], b), hb_byte(Dw[k], b),
+                       hb_byte(Lw, b), hb_byte(Rw, b), uw[b], A.q, sW, m);
+      Nw[k] = pack4(s[0], s[1], s[2], s[3]);
+    }
     if (COUNTS) {
       // 16 x (neighbours unequal to the new spin) per byte
-      const uint32_t nf16 = ne16_sum4<8>(Nw[k] ^ w.Up[k], Nw[k] ^ Dw[k],
-                                         Nw[k] ^ Cw[k], Nw[k] ^ Wd[k]);
+      const uint32_t nf16 = ne16_sum4<QB>(Nw[k] ^ w.Up[k], Nw[k] ^ Dw[k],
+                                          Nw[k] ^ Cw[k], Nw[k] ^ Wd[k]);
       ne_acc += __umulhi(nf16, 1u << 28);
     }
   }
@@ -152,7 +232,7 @@ __device__ __forceinline__ void hb_row(const PassArgs &A, const PhiloxKey &ks,
 }
 
 // walk_column with the heat-bath rule.
-template <int COLOUR, bool COUNTS, bool PAIRS, int LAY>
+template <int QB, int COLOUR, bool COUNTS, bool PAIRS, int LAY>
 __device__ __forceinline__ void hb_walk_column(
     const PassArgs &A, const PhiloxKey &ks, const uint32_t *sW, uint32_t m,
     int32_t x0, int32_t i0, int32_t rows, uint32_t *lane_hist,
@@ -177,11 +257,11 @@ __device__ __forceinline__ void hb_walk_column(
   int32_t r = 0;
   if ((i0 & 1) == 0) {
     for (; r + 2 <= rows; r += 2) {
-      hb_row<COLOUR == 0, COUNTS, PAIRS, LAY>(A, ks, sW, m, w, x0, xb, xl, xr,
-                                              RB, true, lane_hist, ne_acc);
-      hb_row<COLOUR == 1, COUNTS, PAIRS, LAY>(A, ks, sW, m, w, x0, xb, xl, xr,
-                                              RB, r + 2 < rows, lane_hist,
-                                              ne_acc);
+      hb_row<QB, COLOUR == 0, COUNTS, PAIRS, LAY>(
+          A, ks, sW, m, w, x0, xb, xl, xr, RB, true, lane_hist, ne_acc);
+      hb_row<QB, COLOUR == 1, COUNTS, PAIRS, LAY>(
+          A, ks, sW, m, w, x0, xb, xl, xr, RB, r + 2 < rows, lane_hist,
+          ne_acc);
       if (COUNTS) {
         *ne_total += (ne_acc * 0x01010101u) >> 24;
         ne_acc = 0;
@@ -191,11 +271,12 @@ __device__ __forceinline__ void hb_walk_column(
   for (; r < rows; ++r) {
     const bool left = ((w.i + COLOUR) & 1) == 0;
     if (left)
-      hb_row<true, COUNTS, PAIRS, LAY>(A, ks, sW, m, w, x0, xb, xl, xr, RB,
-                                       r + 1 < rows, lane_hist, ne_acc);
+      hb_row<QB, true, COUNTS, PAIRS, LAY>(A, ks, sW, m, w, x0, xb, xl, xr,
+                                           RB, r + 1 < rows, lane_hist, ne_acc);
     else
-      hb_row<false, COUNTS, PAIRS, LAY>(A, ks, sW, m, w, x0, xb, xl, xr, RB,
-                                        r + 1 < rows, lane_hist, ne_acc);
+      hb_row<QB, false, COUNTS, PAIRS, LAY>(A, ks, sW, m, w, x0, xb, xl, xr,
+                                            RB, r + 1 < rows, lane_hist,
+                                            ne_acc);
     if (COUNTS) {
       *ne_total += (ne_acc * 0x01010101u) >> 24;
       ne_acc = 0;
