@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(kPassThreads,
   A.t_hi = (uint32_t)(t0 >> 32);
   A.key0 = d.key0;
   A.key1 = d.key1;
+  A.one = 1u;
   A.hist_bins = q;
   A.layout = kLayoutU8;
   const PhiloxKey ks = philox_schedule(A.key0, A.key1);

@@ -292,6 +292,7 @@ int potts_sweep(potts_h h, double beta, int64_t nsweeps, uint64_t *out_counts) {
     A[c].colour = (uint32_t)c;
     A[c].key0 = (uint32_t)h->seed;
     A[c].key1 = (uint32_t)(h->seed >> 32);
+    A[c].one = 1u;
     A[c].hist_bins = (uint32_t)q;
     A[c].layout = (uint32_t)h->layout;
   }

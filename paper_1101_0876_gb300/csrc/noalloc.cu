@@ -93,6 +93,7 @@ extern "C" int potts_sweep_planes_noalloc(void *white, void *black, int32_t L,
     A[c].key1 = (uint32_t)(seed >> 32);
     // the planes are the caller's and unchecked: a byte >= q must not
     // index outside the shared histogram
+    A[c].one = 1u;
     A[c].hist_bins = 256u;
     A[c].layout = kLayoutU8;
   }
