@@ -89,19 +89,25 @@ __device__ __forceinline__ uint32_t hb_ge(uint32_t a, uint32_t b) {
 // unheld-state index moved past the held states by their ranks instead of
 // a sort (the idx-th unheld state is idx + #{held d : d - rank(d) <= idx}).
 // U, D, Lw, Rw: neighbour words (up, down, left, right); uw: Philox words.
+// one: the run-time 1 of PassArgs, so the six byte additions issue as
+// multiply-adds on the FMA-heavy pipe (the ALU pipe is the busy one here).
 template <int QB>
 __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
                                             uint32_t Lw, uint32_t Rw,
                                             const uint32_t uw[4], uint32_t q,
-                                            const uint32_t *sW, uint32_t m) {
+                                            const uint32_t *sW, uint32_t m,
+                                            uint32_t one) {
   static_assert(QB <= 6, "byte sums below need spins < 64");
   constexpr uint32_t K = Swar<QB>::K, M = Swar<QB>::M;
   constexpr uint32_t ONE = 0x01010101u, FIVE = 0x05050505u;
   constexpr uint32_t SENT = 0x7F7F7F7Fu;  // above every state < 64
   // 2^QB per byte where two neighbours are equal
-  const uint32_t E01 = ~((U ^ D) + K) & M, E02 = ~((U ^ Lw) + K) & M;
-  const uint32_t E03 = ~((U ^ Rw) + K) & M, E12 = ~((D ^ Lw) + K) & M;
-  const uint32_t E13 = ~((D ^ Rw) + K) & M, E23 = ~((Lw ^ Rw) + K) & M;
+  const uint32_t E01 = ~((U ^ D) * one + K) & M;
+  const uint32_t E02 = ~((U ^ Lw) * one + K) & M;
+  const uint32_t E03 = ~((U ^ Rw) * one + K) & M;
+  const uint32_t E12 = ~((D ^ Lw) * one + K) & M;
+  const uint32_t E13 = ~((D ^ Rw) * one + K) & M;
+  const uint32_t E23 = ~((Lw ^ Rw) * one + K) & M;
   // first appearances (1 per byte) and their byte masks
   const uint32_t F1 = (E01 ^ M) >> QB;
   const uint32_t F2 = (~(E02 | E12) & M) >> QB;
@@ -197,7 +203,7 @@ __device__ __forceinline__ void hb_row(const PassArgs &A, const PhiloxKey &ks,
     const uint32_t Lw = LEFT ? Wd[k] : Cw[k];
     const uint32_t Rw = LEFT ? Cw[k] : Wd[k];
     if constexpr (QB <= 6) {
-      Nw[k] = hb_word<QB>(w.Up[k], Dw[k], Lw, Rw, uw, A.q, sW, m);
+      Nw[k] = hb_word<QB>(w.Up[k], Dw[k], Lw, Rw, uw, A.q, sW, m, A.one);
     } else {
       uint32_t s[4];
 #pragma unroll
