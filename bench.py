@@ -109,6 +109,27 @@ def instructions_per_site():
             "source": "profiles/colour_pass_L16384_q9.md (ncu, L = 16384)"}
 
 
+# GB300 instruction issue: one warp instruction per clock on each of the
+# four sub-partitions of an SM, 32 threads, 152 SMs, 2.07 GHz maximum SM clock.
+ISSUE_PEAK = 4 * 32 * 152 * 2.07e9   # thread instructions per second
+
+
+def alu_roofline(sites_per_s: float):
+    """The integer-issue roofline of the colour pass: thread instructions
+    per second (sites/s x instructions per site, the latter from the
+    committed ncu summary, mean of the two passes) against the issue peak."""
+    ips = instructions_per_site()
+    if ips is None:
+        return None
+    per_site = 0.5 * (ips["white"] + ips["black"])
+    achieved = sites_per_s * per_site
+    return {"bound": "alu", "achieved": achieved, "peak": ISSUE_PEAK,
+            "unit": "thread instructions/s", "frac": achieved / ISSUE_PEAK,
+            "inst_per_site": per_site,
+            "peak_source": "4 warp instructions per clock per SM x 32 x 152 "
+                           "SMs x 2.07 GHz"}
+
+
 # ------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
@@ -388,6 +409,7 @@ def run_ours(args):
                      "kernel": "colour pass (white; black fused with counts)",
                      "bytes_per_launch": bytes_per_launch,
                      "inst_per_site": instructions_per_site()},
+        "roofline_alu": alu_roofline(N * K / (dev_ms * 1e-3)),
         "clocks": clocks.summary(),
     }
     if ws == 1 and not args.no_u4:
