@@ -26,6 +26,8 @@ Metric: ns per spin update (time / (N * sweeps)), whole job, lower is better.
   cpu_baseline  the serial CPU oracle on a bounded sample (one core), plus
                 one oracle instance per host core (aggregate).
   heatbath      the same workload with the heat-bath update rule.
+  fused         the same workload under the fused sweep schedule (both
+                colour passes in one kernel, 2 bytes per spin per sweep).
 
 With torchrun (N > 1) each rank sweeps its own replica (weak scaling, no
 data-path collective); the time is the max over ranks.
@@ -418,6 +420,9 @@ def run_ours(args):
     if ws == 1 and not args.no_heatbath:
         lat.close()
         line["heatbath"] = measure_heatbath(args, L, q, betas)
+    if ws == 1 and not args.no_fused:
+        lat.close()
+        line["fused"] = measure_fused(args, L, q, betas, ns)
     if ws == 1 and not args.no_batched:
         lat.close()
         line["batched"] = measure_batched(args, line["updates_per_s"])
@@ -499,6 +504,39 @@ def measure_heatbath(args, L, q, betas):
     return {"value": ms * 1e6 / (N * n), "unit": UNIT, "sweeps": n,
             "updates_per_s": N * n / (ms * 1e-3), "achieved_gbs": gbs,
             "frac_hbm": gbs / hbm}
+
+
+# ------------------------------------------------ fused sweep schedule
+def measure_fused(args, L, q, betas, two_pass_ns):
+    """The same workload (U8, Metropolis) with both colour passes of a sweep
+    in one kernel: each plane read once (plus halos) and written once, 2
+    bytes per site per sweep.  Device-timed like `value`."""
+    import torch
+    from paper_1101_0876_gb300 import potts
+    stream = torch.cuda.Stream()
+    lat = potts.Lattice(L, q, potts.START_RANDOM, 11, layout=potts.LAYOUT_U8)
+    lat.set_schedule(potts.SCHEDULE_FUSED)
+    lat.set_stream(stream.cuda_stream)
+    lat.sweep(betas[0], 3, records=False)
+    n = max(3, args.steps // 2)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.sweep(betas[1], n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    lat.close()
+    N = L * L
+    hbm, _ = measured_peaks()
+    gbs = 2.0 * N * n / (ms * 1e-3) / 1e9
+    ns = ms * 1e6 / (N * n)
+    return {"value": ns, "unit": UNIT, "sweeps": n,
+            "updates_per_s": N * n / (ms * 1e-3),
+            "bytes_per_update": 2.0, "achieved_gbs": gbs,
+            "frac_hbm": gbs / hbm, "vs_two_pass": ns / two_pass_ns,
+            "kernel": "fused_sweep_kernel (one launch per sweep)"}
 
 
 # ------------------------------------------------- batched / served
@@ -653,6 +691,7 @@ def main():
     ap.add_argument("--ref-L", type=int, default=1024)
     ap.add_argument("--no-u4", action="store_true")
     ap.add_argument("--no-heatbath", action="store_true")
+    ap.add_argument("--no-fused", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--batch-sweeps", type=int, default=500)

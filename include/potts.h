@@ -48,7 +48,8 @@
  *     on a handle run on that device and restore the caller's current
  *     device before returning.
  *   - Version 200 (0.2.0) added the heat-bath rule (potts_set_update,
- *     potts_heatbath_weights, potts_batch_set_update, potts_req.update).
+ *     potts_heatbath_weights, potts_batch_set_update, potts_req.update);
+ *     version 210 the fused sweep (potts_set_schedule).
  */
 #ifndef POTTS_H
 #define POTTS_H
@@ -157,6 +158,24 @@ int potts_threshold_table(double beta, uint64_t out_thr[5]);
 enum { POTTS_UPDATE_METROPOLIS = 0, POTTS_UPDATE_HEATBATH = 1 };
 int potts_set_update(potts_h h, int32_t update);
 
+/* Kernel schedule of a Metropolis sweep on a handle.
+ *   POTTS_SCHEDULE_TWO_PASS (default): one kernel per colour pass (Sec. 3:
+ *     the white pass completes before the black pass starts).
+ *   POTTS_SCHEDULE_FUSED: both passes of a sweep in one kernel.  Each CTA
+ *     stages a 32-row x 512-site tile of both colour planes, with halos, in
+ *     shared memory; it updates the white sites of the tile and of a one-site
+ *     halo around it (halo sites are also updated, identically, by the
+ *     neighbouring tiles), then the black sites of the tile against them, and
+ *     writes both planes back once.  Each plane is read and written once per
+ *     sweep instead of being read twice.  Same random words, same rule:
+ *     spins and records are identical to TWO_PASS.
+ * FUSED allocates a second pair of planes (the sweep reads one pair and
+ * writes the other; see potts_device_planes).  The heat-bath rule always
+ * runs two passes.  Errors: EINVAL (unknown schedule; FUSED on a handle
+ * whose layout is not U8 or whose L is not a multiple of 1024), ENOMEM. */
+enum { POTTS_SCHEDULE_TWO_PASS = 0, POTTS_SCHEDULE_FUSED = 1 };
+int potts_set_schedule(potts_h h, int32_t schedule);
+
 /* Heat-bath weights for beta and q: out_W[n] = round(2^m exp(beta n)) for
  * n = 0..4 (so out_W[0] = 2^m), computed on the host in FP64, with *out_m
  * the largest m in 0..31 that keeps the normaliser Z = sum over the q
@@ -172,7 +191,9 @@ int potts_set_stream(potts_h h, void *stream);
 
 /* Device pointers of the two colour planes (white = 0, black = 1), their
  * row pitch in bytes, and the layout, for callers that inspect the device
- * state directly.  Read-only view; owned by the handle. */
+ * state directly.  Read-only view; owned by the handle.  Under the fused
+ * schedule each sweep moves the planes between two buffers, so the pointers
+ * hold until the next potts_sweep. */
 int potts_device_planes(potts_h h, void **white, void **black,
                         int64_t *row_bytes, int32_t *layout);
 

@@ -134,6 +134,17 @@ cudaError_t launch_recount(const uint8_t *white, const uint8_t *black,
                            int32_t L, int32_t H, uint32_t q, uint32_t layout,
                            unsigned long long *rec, cudaStream_t st);
 
+// Both colour passes of one Metropolis sweep in one launch (fused.cu):
+// U8 layout, L a multiple of 1024.  Reads the planes (white, black), writes
+// the swept planes to (white_out, black_out), which must not overlap them;
+// rec (not null, starting at zero) receives the sweep's record {B, hist}.
+bool fused_supported(int32_t L, int32_t q, int32_t layout);
+cudaError_t launch_fused_sweep(const uint8_t *white, const uint8_t *black,
+                               uint8_t *white_out, uint8_t *black_out,
+                               int32_t L, uint32_t q, uint64_t t,
+                               uint64_t seed, const AcceptTable &T,
+                               unsigned long long *rec, cudaStream_t st);
+
 int sm_count_of_current_device();
 
 // FP64 observables of one record.

@@ -141,6 +141,7 @@ struct potts_lattice {
   uint64_t sweep = 0;       // next global sweep index
   int device = 0;
   uint8_t *d_planes = nullptr;  // white plane then black plane
+  uint8_t *d_alt = nullptr;     // second pair the fused sweep writes into
   int64_t plane_bytes = 0;
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
@@ -150,6 +151,7 @@ struct potts_lattice {
   TileGeom geom{};
   potts_obs obs{};
   int32_t update = POTTS_UPDATE_METROPOLIS;
+  int32_t schedule = POTTS_SCHEDULE_TWO_PASS;
 };
 
 static constexpr int64_t kRecordBytesTarget = 4 << 20;
@@ -170,6 +172,7 @@ static int recount_into_obs(potts_h h) {
 static void free_lattice(potts_h h) {
   if (!h) return;
   if (h->d_planes) cudaFree(h->d_planes);
+  if (h->d_alt) cudaFree(h->d_alt);
   if (h->d_rec) cudaFree(h->d_rec);
   if (h->h_rec) cudaFreeHost(h->h_rec);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
@@ -180,7 +183,7 @@ extern "C" {
 
 const char *potts_last_error(void) { return g_err.c_str(); }
 
-int potts_version(void) { return 200; }
+int potts_version(void) { return 210; }
 
 int potts_threshold_table(double beta, uint64_t out_thr[5]) {
   if (!out_thr) return fail(POTTS_EINVAL, "out_thr is NULL");
@@ -302,6 +305,15 @@ int potts_sweep(potts_h h, double beta, int64_t nsweeps, uint64_t *out_counts) {
     POTTS_CK(cudaMemsetAsync(h->d_rec, 0, (size_t)(n * rec_len * 8), h->stream));
     for (int64_t s = 0; s < n; ++s) {
       const uint64_t t = h->sweep + (uint64_t)s;
+      if (!hb && h->schedule == POTTS_SCHEDULE_FUSED) {
+        const int64_t pb = h->plane_bytes;
+        POTTS_CK(launch_fused_sweep(h->d_planes, h->d_planes + pb, h->d_alt,
+                                    h->d_alt + pb, h->L, (uint32_t)q, t,
+                                    h->seed, T, h->d_rec + s * rec_len,
+                                    h->stream));
+        std::swap(h->d_planes, h->d_alt);
+        continue;
+      }
       for (int c = 0; c < 2; ++c) {
         A[c].t_lo = (uint32_t)t;
         A[c].t_hi = (uint32_t)(t >> 32);
@@ -333,6 +345,27 @@ int potts_set_update(potts_h h, int32_t update) {
   if (update != POTTS_UPDATE_METROPOLIS && update != POTTS_UPDATE_HEATBATH)
     return fail(POTTS_EINVAL, "unknown update rule %d", update);
   h->update = update;
+  return POTTS_OK;
+}
+
+int potts_set_schedule(potts_h h, int32_t schedule) {
+  if (!h) return fail(POTTS_EINVAL, "handle is NULL");
+  if (schedule != POTTS_SCHEDULE_TWO_PASS && schedule != POTTS_SCHEDULE_FUSED)
+    return fail(POTTS_EINVAL, "unknown sweep schedule %d", schedule);
+  if (schedule == POTTS_SCHEDULE_FUSED &&
+      !fused_supported(h->L, h->q, h->layout))
+    return fail(POTTS_EINVAL,
+                "the fused sweep needs the U8 layout and L a multiple of 1024 "
+                "(L=%d, layout=%d)", h->L, h->layout);
+  if (schedule == POTTS_SCHEDULE_FUSED && !h->d_alt) {
+    DeviceScope device_scope(h->device);
+    if (cudaMalloc(&h->d_alt, (size_t)(2 * h->plane_bytes)) != cudaSuccess) {
+      h->d_alt = nullptr;
+      return fail(POTTS_ENOMEM, "cannot allocate the fused sweep's planes "
+                  "(%lld bytes)", (long long)(2 * h->plane_bytes));
+    }
+  }
+  h->schedule = schedule;
   return POTTS_OK;
 }
 

@@ -18,6 +18,7 @@ START_ORDERED, START_RANDOM = 0, 1
 LAYOUT_AUTO, LAYOUT_U8, LAYOUT_U4 = 0, 1, 2
 UPDATE_METROPOLIS, UPDATE_HEATBATH = 0, 1
 ADMIT_FIFO, ADMIT_SMALLEST = 0, 1
+SCHEDULE_TWO_PASS, SCHEDULE_FUSED = 0, 1
 
 _u8p = ctypes.POINTER(ctypes.c_uint8)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -79,6 +80,7 @@ _SIGS = {
     "potts_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double,
                                    ctypes.c_int64, _u64p]),
     "potts_set_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "potts_set_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "potts_batch_set_update": (ctypes.c_int, [
         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
     "potts_heatbath_weights": (ctypes.c_int, [
@@ -247,6 +249,12 @@ class Lattice:
         """UPDATE_METROPOLIS (default) or UPDATE_HEATBATH for later
         sweeps."""
         check(lib().potts_set_update(self._h, int(update)))
+
+    def set_schedule(self, schedule: int) -> None:
+        """SCHEDULE_TWO_PASS (default) or SCHEDULE_FUSED (one kernel per
+        Metropolis sweep; U8 layout, L a multiple of 1024) for later
+        sweeps."""
+        check(lib().potts_set_schedule(self._h, int(schedule)))
 
     def observables(self) -> dict:
         o = PottsObs()
