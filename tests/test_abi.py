@@ -100,3 +100,17 @@ def test_binding_refuses_to_run_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(potts, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         potts.lib()
+
+
+def test_binding_constants_equal_header_enums(libpotts):
+    text = open(os.path.join(ROOT, "include", "potts.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    values = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+        for name, val in re.findall(r"(POTTS_\w+)\s*=\s*(\d+)", body):
+            values[name] = int(val)
+    assert len(values) >= 19
+    for name, val in values.items():
+        short = name[len("POTTS_"):]
+        got = getattr(libpotts, name, getattr(libpotts, short, None))
+        assert got == val, (name, got, val)
