@@ -584,17 +584,8 @@ int Engine::drain() {
 }
 
 int Engine::copy_spins(const Member *m, uint8_t *out_LxL) {
-  std::vector<uint8_t> tmp;
-  try {
-    tmp.resize((size_t)(2 * m->plane_bytes));
-  } catch (...) {
-    return fail(POTTS_ENOMEM, "host allocation failed");
-  }
-  POTTS_CK(cudaMemcpyAsync(tmp.data(), m->planes, tmp.size(),
-                           cudaMemcpyDeviceToHost, st_));
-  POTTS_CK(cudaStreamSynchronize(st_));
-  planes_to_rowmajor(tmp.data(), tmp.data() + m->plane_bytes, m->L, out_LxL);
-  return POTTS_OK;
+  return download_rowmajor(m->planes, m->planes + m->plane_bytes, m->L,
+                           kLayoutU8, out_LxL, st_);
 }
 
 // Times candidate (rows per walk, sweeps per graph) pairs on a scratch copy

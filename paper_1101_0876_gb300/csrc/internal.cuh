@@ -151,11 +151,14 @@ int sm_count_of_current_device();
 void update_obs(potts_obs *obs, const uint64_t *rec, int32_t L, int32_t q,
                 bool accumulate);
 
-// Host-side (de)interleaving between the row-major L x L layout and the two
-// colour planes (L rows x H bytes each).
-void planes_to_rowmajor(const uint8_t *white, const uint8_t *black, int32_t L,
-                        uint8_t *out);
-void rowmajor_to_planes(const uint8_t *in, int32_t L, uint8_t *white,
-                        uint8_t *black);
+// Spins between the caller's row-major L x L host bytes and the colour
+// planes (layout.cu), through a device staging buffer and conversion
+// kernels on stream st; both synchronise st.  upload_rowmajor writes the
+// planes only if every spin is < q (else POTTS_EINVAL).  Return POTTS_*.
+int download_rowmajor(const uint8_t *white, const uint8_t *black, int32_t L,
+                      uint32_t layout, uint8_t *out_LxL, cudaStream_t st);
+int upload_rowmajor(const uint8_t *in_LxL, int32_t L, uint32_t q,
+                    uint32_t layout, uint8_t *white, uint8_t *black,
+                    cudaStream_t st);
 
 }  // namespace potts

@@ -89,47 +89,6 @@ void update_obs(potts_obs *obs, const uint64_t *rec, int32_t L, int32_t q,
   }
 }
 
-void planes_to_rowmajor(const uint8_t *white, const uint8_t *black, int32_t L,
-                        uint8_t *out) {
-  const int64_t H = L / 2;
-  for (int64_t i = 0; i < L; ++i) {
-    const uint8_t *w = white + i * H, *b = black + i * H;
-    uint8_t *o = out + i * L;
-    if ((i & 1) == 0) {
-      for (int64_t x = 0; x < H; ++x) { o[2 * x] = w[x]; o[2 * x + 1] = b[x]; }
-    } else {
-      for (int64_t x = 0; x < H; ++x) { o[2 * x] = b[x]; o[2 * x + 1] = w[x]; }
-    }
-  }
-}
-
-void rowmajor_to_planes(const uint8_t *in, int32_t L, uint8_t *white,
-                        uint8_t *black) {
-  const int64_t H = L / 2;
-  for (int64_t i = 0; i < L; ++i) {
-    uint8_t *w = white + i * H, *b = black + i * H;
-    const uint8_t *s = in + i * L;
-    if ((i & 1) == 0) {
-      for (int64_t x = 0; x < H; ++x) { w[x] = s[2 * x]; b[x] = s[2 * x + 1]; }
-    } else {
-      for (int64_t x = 0; x < H; ++x) { b[x] = s[2 * x]; w[x] = s[2 * x + 1]; }
-    }
-  }
-}
-
-// U4 plane (L rows x L/4 bytes, site 2b in the low nibble of byte b) <->
-// U8 plane (L rows x L/2 bytes).
-static void u4_to_u8(const uint8_t *in, int64_t nbytes, uint8_t *out) {
-  for (int64_t b = 0; b < nbytes; ++b) {
-    out[2 * b] = in[b] & 0x0F;
-    out[2 * b + 1] = in[b] >> 4;
-  }
-}
-static void u8_to_u4(const uint8_t *in, int64_t nbytes, uint8_t *out) {
-  for (int64_t b = 0; b < nbytes; ++b)
-    out[b] = (uint8_t)((in[2 * b] & 0x0F) | (in[2 * b + 1] << 4));
-}
-
 }  // namespace potts
 
 using namespace potts;
@@ -387,63 +346,17 @@ int potts_reset_averages(potts_h h) {
 int potts_get_spins(potts_h h, uint8_t *out_LxL) {
   if (!h || !out_LxL) return fail(POTTS_EINVAL, "NULL argument");
   DeviceScope device_scope(h->device);
-  std::vector<uint8_t> tmp;
-  try {
-    tmp.resize((size_t)(2 * h->plane_bytes));
-  } catch (...) {
-    return fail(POTTS_ENOMEM, "host allocation failed");
-  }
-  POTTS_CK(cudaMemcpyAsync(tmp.data(), h->d_planes, tmp.size(),
-                           cudaMemcpyDeviceToHost, h->stream));
-  POTTS_CK(cudaStreamSynchronize(h->stream));
-  if (h->layout == POTTS_LAYOUT_U4) {
-    std::vector<uint8_t> u8;
-    const int64_t sites = (int64_t)h->L * h->H;
-    try {
-      u8.resize((size_t)(2 * sites));
-    } catch (...) {
-      return fail(POTTS_ENOMEM, "host allocation failed");
-    }
-    u4_to_u8(tmp.data(), h->plane_bytes, u8.data());
-    u4_to_u8(tmp.data() + h->plane_bytes, h->plane_bytes, u8.data() + sites);
-    planes_to_rowmajor(u8.data(), u8.data() + sites, h->L, out_LxL);
-  } else {
-    planes_to_rowmajor(tmp.data(), tmp.data() + h->plane_bytes, h->L, out_LxL);
-  }
-  return POTTS_OK;
+  return download_rowmajor(h->d_planes, h->d_planes + h->plane_bytes, h->L,
+                           (uint32_t)h->layout, out_LxL, h->stream);
 }
 
 int potts_set_state(potts_h h, const uint8_t *LxL, uint64_t sweep) {
   if (!h || !LxL) return fail(POTTS_EINVAL, "NULL argument");
   DeviceScope device_scope(h->device);
-  const int64_t n = (int64_t)h->L * h->L;
-  for (int64_t k = 0; k < n; ++k)
-    if (LxL[k] >= h->q)
-      return fail(POTTS_EINVAL, "spin %d at %lld is >= q = %d", LxL[k],
-                  (long long)k, h->q);
-  std::vector<uint8_t> tmp;
-  try {
-    tmp.resize((size_t)(2 * h->plane_bytes));
-  } catch (...) {
-    return fail(POTTS_ENOMEM, "host allocation failed");
-  }
-  if (h->layout == POTTS_LAYOUT_U4) {
-    std::vector<uint8_t> u8;
-    const int64_t sites = (int64_t)h->L * h->H;
-    try {
-      u8.resize((size_t)(2 * sites));
-    } catch (...) {
-      return fail(POTTS_ENOMEM, "host allocation failed");
-    }
-    rowmajor_to_planes(LxL, h->L, u8.data(), u8.data() + sites);
-    u8_to_u4(u8.data(), h->plane_bytes, tmp.data());
-    u8_to_u4(u8.data() + sites, h->plane_bytes, tmp.data() + h->plane_bytes);
-  } else {
-    rowmajor_to_planes(LxL, h->L, tmp.data(), tmp.data() + h->plane_bytes);
-  }
-  POTTS_CK(cudaMemcpyAsync(h->d_planes, tmp.data(), tmp.size(),
-                           cudaMemcpyHostToDevice, h->stream));
-  POTTS_CK(cudaStreamSynchronize(h->stream));
+  const int rc = upload_rowmajor(LxL, h->L, (uint32_t)h->q,
+                                 (uint32_t)h->layout, h->d_planes,
+                                 h->d_planes + h->plane_bytes, h->stream);
+  if (rc) return rc;
   h->sweep = sweep;
   h->obs.sweep = sweep;
   return recount_into_obs(h);

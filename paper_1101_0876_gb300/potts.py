@@ -264,8 +264,13 @@ class Lattice:
     def reset_averages(self) -> None:
         check(lib().potts_reset_averages(self._h))
 
-    def spins(self) -> np.ndarray:
-        out = np.empty((self.L, self.L), dtype=np.uint8)
+    def spins(self, out: np.ndarray | None = None) -> np.ndarray:
+        """Row-major L x L spins; into `out` (C-contiguous uint8, e.g. a
+        pinned buffer) when given."""
+        if out is None:
+            out = np.empty((self.L, self.L), dtype=np.uint8)
+        assert out.dtype == np.uint8 and out.flags.c_contiguous
+        assert out.size == self.L * self.L
         check(lib().potts_get_spins(self._h, _ptr(out, ctypes.c_uint8)))
         return out
 
