@@ -72,14 +72,13 @@ __device__ __forceinline__ void fused_chunk(
     const uint64_t r2 = (uint64_t)u.z * q, r3 = (uint64_t)u.w * q;
     const uint32_t P = pack4((uint32_t)(r0 >> 32), (uint32_t)(r1 >> 32),
                              (uint32_t)(r2 >> 32), (uint32_t)(r3 >> 32));
-    uint32_t no16 = 0;
-    const uint32_t idx =
-        delta_index<QB, COUNTS>(S[k], P, U[k], D[k], C[k], Wd[k], &no16, one);
+    uint32_t no16 = 0, nn16 = 0;
+    const uint32_t idx = delta_index<QB, COUNTS>(S[k], P, U[k], D[k], C[k],
+                                                 Wd[k], &no16, &nn16, one);
     const uint32_t m = accept_mask<LT0>(idx, (uint32_t)r0, (uint32_t)r1,
                                         (uint32_t)r2, (uint32_t)r3, tab);
     N[k] = (P & m) | (S[k] & ~m);
     if (COUNTS) {
-      const uint32_t nn16 = idx + no16 - 0x40404040u;
       const uint32_t nf16 = (nn16 & m) | (no16 & ~m);
       ne_acc += __umulhi(nf16, 1u << 28);
     }
@@ -235,17 +234,12 @@ cudaError_t launch_fused_k(const uint8_t *white, const uint8_t *black,
                            int32_t H, uint32_t q, uint64_t t, uint64_t seed,
                            const AcceptTable &T, unsigned long long *rec,
                            cudaStream_t st) {
-  static int attr_dev = -1;  // device the attribute was last set on
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  // set on every launch (a host-side call): handles may run on several
+  // devices and threads
+  const cudaError_t e = cudaFuncSetAttribute(
+      fused_sweep_kernel<QB, PAIRS, LT0>,
+      cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmemMax);
   if (e != cudaSuccess) return e;
-  if (attr_dev != dev) {
-    e = cudaFuncSetAttribute(fused_sweep_kernel<QB, PAIRS, LT0>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kFSmemMax);
-    if (e != cudaSuccess) return e;
-    attr_dev = dev;
-  }
   const dim3 grid((unsigned)(H / 16 / kFTW), (unsigned)(L / kFR));
   const size_t smem = (size_t)kWBytes + kBBytes +
                       (size_t)(PAIRS ? kFPairBins : q) * 32u * 4u;

@@ -65,12 +65,12 @@ struct AcceptTable {
 // ---------------------------------------------------------------- SWAR
 //
 // Per site the decision needs idx = 16 * (4 + dE) (dE = n_old - n_new).
-// With NE_x = [x != neighbour] and EQ_x = [x == neighbour], each neighbour
-// contributes c = NE_new + EQ_old in {0, 1, 2} and the four contributions
-// add up to 4 - n_new + n_old = 4 + dE.  For spins < 2^QB, a = (S ^ N) +
-// (2^QB - 1) holds EQ_old in bit QB inverted and b = (P ^ N) + (2^QB - 1)
-// holds NE_new in bit QB, so c = ((b | ~a) & M) + ((b & ~a) & M) with
-// M = 2^QB per byte (two 3-input logic ops per neighbour, no shifts).
+// For spins < 2^QB, a = (S ^ N) + (2^QB - 1) holds [S != N] in bit QB and
+// b = (P ^ N) + (2^QB - 1) holds [P != N] there, so with M = 2^QB per byte
+// X = sum (b & M) = M (4 - n_new) and Y = sum (a & M) = M (4 - n_old) over
+// the four neighbours, and 4 + dE = 4 + (X - Y) / M: one logic op per
+// (state, neighbour) pair.  Y and X are also the mismatch counts the black
+// pass needs for its bond count (old and proposed state).
 
 template <int QB>
 struct Swar {
@@ -107,7 +107,8 @@ __device__ __forceinline__ uint32_t ne16_sum4(uint32_t x0, uint32_t x1,
 }
 
 // idx = 16 * (4 + dE) per byte for the four sites of one word.  With
-// WANT_NO also *no16 = 16 * (number of neighbours unequal to S).
+// WANT_NO also *no16 = 16 * (number of neighbours unequal to S) and
+// *nn16 = 16 * (number unequal to P).
 // `one` is the constant 1, supplied at run time where the eight additions
 // of K should issue as multiply-adds (x * one + K, which the compiler cannot
 // fold back into additions) on the FMA-heavy pipe instead of the busier ALU
@@ -117,26 +118,33 @@ template <int QB, bool WANT_NO>
 __device__ __forceinline__ uint32_t delta_index(uint32_t S, uint32_t P,
                                                 uint32_t U, uint32_t D,
                                                 uint32_t C, uint32_t W,
-                                                uint32_t *no16, uint32_t one) {
+                                                uint32_t *no16, uint32_t *nn16,
+                                                uint32_t one) {
   if constexpr (QB <= 5) {
     constexpr uint32_t K = Swar<QB>::K, M = Swar<QB>::M;
     const uint32_t a0 = (S ^ U) * one + K, a1 = (S ^ D) * one + K,
                    a2 = (S ^ C) * one + K, a3 = (S ^ W) * one + K;
     const uint32_t b0 = (P ^ U) * one + K, b1 = (P ^ D) * one + K,
                    b2 = (P ^ C) * one + K, b3 = (P ^ W) * one + K;
-    const uint32_t s1 = ((b0 | ~a0) & M) + ((b1 | ~a1) & M) +
-                        ((b2 | ~a2) & M) + ((b3 | ~a3) & M);
-    const uint32_t s2 = ((b0 & ~a0) & M) + ((b1 & ~a1) & M) +
-                        ((b2 & ~a2) & M) + ((b3 & ~a3) & M);
-    if (WANT_NO) {
-      const uint32_t n = (a0 & M) + (a1 & M) + (a2 & M) + (a3 & M);
-      *no16 = QB == 4 ? n : n >> 1;
+    // per byte at most 4 M = 64 (QB 4) or 128 (QB 5): no carry between bytes
+    uint32_t X = (b0 & M) + (b1 & M) + (b2 & M) + (b3 & M);
+    uint32_t Y = (a0 & M) + (a1 & M) + (a2 & M) + (a3 & M);
+    if (QB == 5) {  // multiples of 32 per byte: the shift moves no bit across
+      X >>= 1;
+      Y >>= 1;
     }
-    return QB == 4 ? s1 + s2 : (s1 >> 1) + (s2 >> 1);
+    if (WANT_NO) {
+      *no16 = Y;
+      *nn16 = X;
+    }
+    return (X + 0x40404040u) - Y;  // X + 64 >= Y per byte: no borrow
   } else {
     const uint32_t no = ne16_sum4<QB>(S ^ U, S ^ D, S ^ C, S ^ W);
     const uint32_t nn = ne16_sum4<QB>(P ^ U, P ^ D, P ^ C, P ^ W);
-    if (WANT_NO) *no16 = no;
+    if (WANT_NO) {
+      *no16 = no;
+      *nn16 = nn;
+    }
     return 0x40404040u + nn - no;
   }
 }
@@ -307,18 +315,18 @@ __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
     const uint64_t r2 = (uint64_t)u.z * A.q, r3 = (uint64_t)u.w * A.q;
     const uint32_t P = pack4((uint32_t)(r0 >> 32), (uint32_t)(r1 >> 32),
                              (uint32_t)(r2 >> 32), (uint32_t)(r3 >> 32));
-    uint32_t no16 = 0;
+    uint32_t no16 = 0, nn16 = 0;
     // the white pass moves its additions to the FMA-heavy pipe; the black
     // pass, whose counts already add multiply-adds, keeps them on the ALU
     // (1.2930 against 1.2893 ps per update at L = 32768)
-    const uint32_t idx = delta_index<QB, COUNTS>(
-        w.S[k], P, w.Up[k], Dw[k], Cw[k], Wd[k], &no16, COUNTS ? 1u : A.one);
+    const uint32_t idx =
+        delta_index<QB, COUNTS>(w.S[k], P, w.Up[k], Dw[k], Cw[k], Wd[k], &no16,
+                                &nn16, COUNTS ? 1u : A.one);
     const uint32_t m = accept_mask<LT0>(idx, (uint32_t)r0, (uint32_t)r1,
                                         (uint32_t)r2, (uint32_t)r3, tab);
     Nw[k] = (P & m) | (w.S[k] & ~m);
     if (COUNTS) {
-      // unequal neighbours after the update: NE_new where accepted
-      const uint32_t nn16 = idx + no16 - 0x40404040u;
+      // unequal neighbours after the update: those of P where accepted
       const uint32_t nf16 = (nn16 & m) | (no16 & ~m);
       ne_acc += __umulhi(nf16, 1u << 28);  // += nf16 >> 4 (<= 4 per byte)
     }
