@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(kPassThreads,
   constexpr bool COUNTS = COLOUR == 1;
   constexpr bool LT0 = KIND == kKindLT0;
   extern __shared__ uint32_t s_hist[];
-  __shared__ __align__(16) uint32_t s_tab[kTabWords];
+  __shared__ __align__(16) uint32_t s_tab[KIND == kKindHB ? kHbTableWords
+                                                          : kTabWords];
   __shared__ uint32_t s_sat;
   const uint32_t tid = threadIdx.x;
   const int32_t bid = (int32_t)blockIdx.x;
@@ -77,15 +78,16 @@ __global__ void __launch_bounds__(kPassThreads,
   const StepDesc &sd = S[d.step];
   if (s >= sd.nsweeps) return;  // same for the whole CTA
   const uint32_t q = (uint32_t)d.q;
-  if (KIND == kKindHB) {
-    if (tid < 8) s_tab[tid] = sd.tab[tid];  // W[0..7]
-  } else {
+  if (KIND != kKindHB) {
     for (uint32_t i = tid; i < (uint32_t)kTabWords; i += kPassThreads)
       s_tab[i] = (i % 4u == 0 && i / 4u < 9u) ? sd.tab[i / 4u] : 0u;
   }
   for (uint32_t v = tid; v < q * 32u; v += kPassThreads) s_hist[v] = 0;
   if (tid == 0) s_sat = 0;
-  __syncthreads();
+  if (KIND == kKindHB)
+    hb_build_table(s_tab, sd.tab, q, sd.tab[8], tid);  // W[0..7], m; barrier
+  else
+    __syncthreads();
   pdl_wait_previous();
 
   PassArgs A;

@@ -27,19 +27,18 @@ __global__ void __launch_bounds__(kPassThreads, QB <= 6 ? 4 : POTTS_HB_MINB)
                    unsigned long long *rec) {
   constexpr bool COUNTS = COLOUR == 1;
   extern __shared__ uint32_t s_hist[];
-  __shared__ uint32_t s_W[8];
+  __shared__ __align__(16) uint32_t s_W[kHbTableWords];
   __shared__ uint32_t s_sat;
   __shared__ uint32_t s_fold[16];
   const uint32_t tid = threadIdx.x;
   const uint32_t bins = PAIRS ? (uint32_t)kHbPairBins : A.hist_bins;
   const bool hist = rec != nullptr;
-  if (tid < 8) s_W[tid] = T.W[tid];
   if (hist) {
     for (uint32_t v = tid; v < bins * 32u; v += kPassThreads) s_hist[v] = 0;
     if (tid < 16) s_fold[tid] = 0;
     if (tid == 0) s_sat = 0;
   }
-  __syncthreads();
+  hb_build_table(s_W, T.W, A.q, T.m, tid);  // ends with a barrier
   pdl_wait_previous();
 
   const PhiloxKey ks = philox_schedule(A.key0, A.key1);

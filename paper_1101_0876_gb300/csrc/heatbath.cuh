@@ -26,6 +26,51 @@ struct HeatTable {
   uint32_t m;
 };
 
+// Shared table of a heat-bath launch: W[0..7], then one 8-word entry per
+// equality pattern of the four neighbours.  The pattern code of a site has
+// bit 0..5 = [up == down], [up == left], [up == right], [down == left],
+// [down == right], [left == right]; the interval bounds s1..s4 (cumulative
+// widths of the neighbour classes in first-appearance order) and the
+// normaliser Z depend on the site only through that code (and on W, q, m,
+// which are fixed for a launch).  Entry: {s1, s2, s3, s4, Z, 0, 0, 0}.  Of
+// the 64 codes only the 15 that are transitive occur.
+constexpr int kHbTableWords = 8 + 64 * 8;
+
+// Fills entry `code` from W (sW[0..7], already in shared memory).
+__device__ __forceinline__ void hb_pattern_entry(uint32_t *sW, uint32_t code,
+                                                 uint32_t q, uint32_t m) {
+  const uint32_t e01 = code & 1u, e02 = (code >> 1) & 1u,
+                 e03 = (code >> 2) & 1u, e12 = (code >> 3) & 1u,
+                 e13 = (code >> 4) & 1u, e23 = (code >> 5) & 1u;
+  const uint32_t f1 = e01 ^ 1u, f2 = (e02 | e12) ^ 1u,
+                 f3 = (e03 | e13 | e23) ^ 1u;
+  const uint32_t c0 = 1u + e01 + e02 + e03;
+  const uint32_t c1 = f1 ? 1u + e12 + e13 : 5u;
+  const uint32_t c2 = f2 ? 1u + e23 : 5u;
+  const uint32_t c3 = f3 ? 1u : 5u;
+  const uint32_t s1 = sW[c0], s2 = s1 + sW[c1], s3 = s2 + sW[c2],
+                 s4 = s3 + sW[c3];
+  const uint32_t k = 1u + f1 + f2 + f3;  // distinct neighbour states
+  uint32_t *e = sW + 8 + 8 * code;
+  e[0] = s1;
+  e[1] = s2;
+  e[2] = s3;
+  e[3] = s4;
+  e[4] = s4 + ((q - k) << m);  // the unheld states, 2^m each
+  e[5] = e[6] = e[7] = 0u;
+}
+
+// Whole table: W from the launch, then the 64 entries.  Every thread of the
+// CTA calls it; it ends with a barrier.
+__device__ __forceinline__ void hb_build_table(uint32_t *sW, const uint32_t *W,
+                                               uint32_t q, uint32_t m,
+                                               uint32_t tid) {
+  if (tid < 8) sW[tid] = W[tid];
+  __syncthreads();
+  if (tid < 64) hb_pattern_entry(sW, tid, q, m);
+  __syncthreads();
+}
+
 __device__ __forceinline__ void hb_cswap(uint32_t &a, uint32_t &b) {
   const uint32_t lo = min(a, b), hi = max(a, b);
   a = lo;
@@ -83,23 +128,34 @@ __device__ __forceinline__ uint32_t hb_ge(uint32_t a, uint32_t b) {
   return (((a | 0x80808080u) - b) & 0x80808080u) >> 7;
 }
 
+// Bit FROM of every byte moved to bit TO.
+template <int FROM, int TO>
+__device__ __forceinline__ uint32_t hb_mv(uint32_t x) {
+  if constexpr (FROM >= TO)
+    return x >> (FROM - TO);
+  else
+    return x << (TO - FROM);
+}
+
 // The four sites of one word at once (spins < 2^QB, QB <= 6): the same
-// rule as hb_site, with the neighbour comparisons, counts, first
-// appearances and weight indices done per byte on whole words, and the
-// unheld-state index moved past the held states by their ranks instead of
-// a sort (the idx-th unheld state is idx + #{held d : d - rank(d) <= idx}).
-// U, D, Lw, Rw: neighbour words (up, down, left, right); uw: Philox words.
+// rule as hb_site, with the neighbour comparisons and first appearances
+// done per byte on whole words, the interval bounds and normaliser read
+// from the pattern table, and the unheld-state index moved past the held
+// states by their ranks instead of a sort (the idx-th unheld state is
+// idx + #{held d : d - rank(d) <= idx}).
+// U, D, Lw, Rw: neighbour words (up, down, left, right); uw: Philox words;
+// sW: the launch's table (hb_build_table).
 // one: the run-time 1 of PassArgs, so the six byte additions issue as
 // multiply-adds on the FMA-heavy pipe (the ALU pipe is the busy one here).
 template <int QB>
 __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
                                             uint32_t Lw, uint32_t Rw,
-                                            const uint32_t uw[4], uint32_t q,
+                                            const uint32_t uw[4],
                                             const uint32_t *sW, uint32_t m,
                                             uint32_t one) {
   static_assert(QB <= 6, "byte sums below need spins < 64");
   constexpr uint32_t K = Swar<QB>::K, M = Swar<QB>::M;
-  constexpr uint32_t ONE = 0x01010101u, FIVE = 0x05050505u;
+  constexpr uint32_t ONE = 0x01010101u;
   constexpr uint32_t SENT = 0x7F7F7F7Fu;  // above every state < 64
   // 2^QB per byte where two neighbours are equal
   const uint32_t E01 = ~((U ^ D) * one + K) & M;
@@ -108,17 +164,15 @@ __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
   const uint32_t E12 = ~((D ^ Lw) * one + K) & M;
   const uint32_t E13 = ~((D ^ Rw) * one + K) & M;
   const uint32_t E23 = ~((Lw ^ Rw) * one + K) & M;
+  // pattern code per byte (bit order of the table)
+  const uint32_t CODE = hb_mv<QB, 0>(E01) | hb_mv<QB, 1>(E02) |
+                        hb_mv<QB, 2>(E03) | hb_mv<QB, 3>(E12) |
+                        hb_mv<QB, 4>(E13) | hb_mv<QB, 5>(E23);
   // first appearances (1 per byte) and their byte masks
   const uint32_t F1 = (E01 ^ M) >> QB;
   const uint32_t F2 = (~(E02 | E12) & M) >> QB;
   const uint32_t F3 = (~(E03 | E13 | E23) & M) >> QB;
   const uint32_t m1 = F1 * 0xFFu, m2 = F2 * 0xFFu, m3 = F3 * 0xFFu;
-  // weight indices: the class's neighbour count, 5 (weight 0) for repeats
-  const uint32_t I0 = ONE + ((E01 + E02 + E03) >> QB);
-  const uint32_t I1 = ((ONE + ((E12 + E13) >> QB)) & m1) | (FIVE & ~m1);
-  const uint32_t I2 = ((ONE + (E23 >> QB)) & m2) | (FIVE & ~m2);
-  const uint32_t I3 = (ONE & m3) | (FIVE & ~m3);
-  const uint32_t KC = ONE + F1 + F2 + F3;  // distinct neighbour states
   // held states (repeats replaced by SENT), their ranks and thresholds
   const uint32_t H1 = (D & m1) | (SENT & ~m1);
   const uint32_t H2 = (Lw & m2) | (SENT & ~m2);
@@ -129,18 +183,17 @@ __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
   const uint32_t T1 = H1 - ((g01 ^ ONE) + g12 + g13);
   const uint32_t T2 = H2 - ((g02 ^ ONE) + (g12 ^ ONE) + g23);
   const uint32_t T3 = H3 - ((g03 ^ ONE) + (g13 ^ ONE) + (g23 ^ ONE));
-  const uint32_t qW0 = q << m;
+  const uint8_t *ent = reinterpret_cast<const uint8_t *>(sW + 8);
   uint32_t idx[4], cls[4];
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
-    const uint32_t w0 = sW[hb_byte(I0, b)], w1 = sW[hb_byte(I1, b)];
-    const uint32_t w2 = sW[hb_byte(I2, b)], w3 = sW[hb_byte(I3, b)];
-    const uint32_t s1 = w0, s2 = s1 + w1, s3 = s2 + w2, s4 = s3 + w3;
-    const uint32_t Z = s4 + qW0 - (hb_byte(KC, b) << m);
+    const uint32_t off = hb_byte(CODE, b) * 32u;
+    const uint4 sb = *reinterpret_cast<const uint4 *>(ent + off);
+    const uint32_t Z = *reinterpret_cast<const uint32_t *>(ent + off + 16);
     const uint32_t r = __umulhi(uw[b], Z);
-    idx[b] = min((r - s4) >> m, 0x40u);  // < q - k <= 62 when used
-    cls[b] = (uint32_t)(r >= s1) + (uint32_t)(r >= s2) + (uint32_t)(r >= s3) +
-             (uint32_t)(r >= s4);
+    idx[b] = min((r - sb.w) >> m, 0x40u);  // < q - k <= 62 when used
+    cls[b] = (uint32_t)(r >= sb.x) + (uint32_t)(r >= sb.y) +
+             (uint32_t)(r >= sb.z) + (uint32_t)(r >= sb.w);
   }
   const uint32_t IDX = pack4(idx[0], idx[1], idx[2], idx[3]);
   const uint32_t CLS = pack4(cls[0], cls[1], cls[2], cls[3]);
@@ -203,7 +256,7 @@ __device__ __forceinline__ void hb_row(const PassArgs &A, const PhiloxKey &ks,
     const uint32_t Lw = LEFT ? Wd[k] : Cw[k];
     const uint32_t Rw = LEFT ? Cw[k] : Wd[k];
     if constexpr (QB <= 6) {
-      Nw[k] = hb_word<QB>(w.Up[k], Dw[k], Lw, Rw, uw, A.q, sW, m, A.one);
+      Nw[k] = hb_word<QB>(w.Up[k], Dw[k], Lw, Rw, uw, sW, m, A.one);
     } else {
       uint32_t s[4];
 #pragma unroll
