@@ -1,8 +1,8 @@
 """Seeded random parity cases (needs a GPU): lattice sizes across the
 geometry rules (one or several CTAs per row, ragged widths, short and long
 walks, one or several tiles per CTA), every spin-width class, both layouts,
-both update rules and the whole range of beta, each checked bit for bit
-against the oracle."""
+both update rules, the fused sweep schedule and the whole range of beta,
+each checked bit for bit against the oracle."""
 import numpy as np
 import pytest
 
@@ -46,4 +46,25 @@ def test_random_case(L, q, start, beta, sweeps, layout, update, seed):
     o = oracle.Lattice(L, q, start, seed)
     assert np.array_equal(g.sweep(beta, sweeps),
                           o.sweep(beta, sweeps, update=update))
+    assert np.array_equal(g.spins(), o.spins())
+
+
+def _fused_cases(n=6, seed=2027):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        L = 1024 * int(rng.integers(1, 3))
+        q = int(rng.choice([2, 3, 9, 16, 17, 31, 40, 100, 256]))
+        beta = float(rng.choice([0.0, rng.uniform(0.2, 3.0), 40.0]))
+        out.append((L, q, int(rng.integers(0, 2)), beta, int(rng.integers(1, 4)),
+                    9000 + i))
+    return out
+
+
+@pytest.mark.parametrize("L,q,start,beta,sweeps,seed", _fused_cases())
+def test_random_fused_case(L, q, start, beta, sweeps, seed):
+    g = potts.Lattice(L, q, start, seed, layout=potts.LAYOUT_U8)
+    g.set_schedule(potts.SCHEDULE_FUSED)
+    o = oracle.Lattice(L, q, start, seed)
+    assert np.array_equal(g.sweep(beta, sweeps), o.sweep(beta, sweeps))
     assert np.array_equal(g.spins(), o.spins())
