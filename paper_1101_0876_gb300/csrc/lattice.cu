@@ -4,7 +4,6 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
-#include <vector>
 
 #include "heatbath.cuh"
 #include "internal.cuh"
