@@ -410,7 +410,9 @@ def run_ours(args):
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "kernel": "colour pass (white; black fused with counts)",
                      "bytes_per_launch": bytes_per_launch,
-                     "inst_per_site": instructions_per_site()},
+                     "inst_per_site": instructions_per_site(),
+                     "binding": "integer instruction issue, not HBM: "
+                                "see roofline_alu"},
         "roofline_alu": alu_roofline(N * K / (dev_ms * 1e-3)),
         "clocks": clocks.summary(),
     }
