@@ -237,3 +237,55 @@ def test_serve_admission_policy(policy):
     for r, (L, n, s) in ((big, (512, 120, 2)), (small, (64, 20, 3))):
         ro, _ = _oracle_run(L, 9, 1, s, 1.0, n)
         assert np.array_equal(np.concatenate(got[r]), ro), r
+
+
+def test_serve_concurrent_clients():
+    """Four host threads submit, poll and cancel on one server at once (the
+    serving calls are thread-safe): every finished request equals the same
+    lattice run alone, the cancelled one reports ECANCELLED, and the
+    server's counts add up."""
+    import threading
+    srv = potts.Server(hbm_budget_bytes=1 << 30, max_slots=3,
+                       sweeps_per_step=4)
+    plans = {t: [(32 + 32 * ((t + k) % 4), [6, 9, 15, 24][(t + 2 * k) % 4],
+                  0.8 + 0.1 * t + 0.05 * k, 10 + 7 * k, 100 * t + k)
+                 for k in range(3)] for t in range(4)}
+    results, errors = {}, []
+
+    def client(t):
+        try:
+            mine = [(srv.submit(L, q, b, n, s), (L, q, b, n, s))
+                    for (L, q, b, n, s) in plans[t]]
+            victim = None
+            if t == 0:  # a long request, cancelled while the others run
+                victim = srv.submit(256, 9, 1.0, 10**7, 999)
+            got = _drain(srv, [r for r, _ in mine])
+            for rid, spec in mine:
+                results[(t, rid)] = (got[rid], spec)
+            if victim is not None:
+                srv.cancel(victim)
+                t0 = time.time()
+                while True:
+                    try:
+                        srv.poll(victim)
+                    except potts.PottsError as e:
+                        assert e.code == potts.POTTS_ECANCELLED
+                        break
+                    assert time.time() - t0 < 30
+                    time.sleep(0.01)
+        except Exception as e:  # reported on the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=client, args=(t,)) for t in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join(timeout=300)
+    st = srv.stats()
+    srv.stop()
+    assert not errors, errors
+    assert len(results) == 12
+    assert st["completed"] == 12 and st["cancelled"] == 1
+    for (t, rid), (rec, (L, q, b, n, s)) in results.items():
+        alone = potts.Lattice(L, q, 1, s).sweep(b, n)
+        assert np.array_equal(rec, alone), (t, rid)
