@@ -175,9 +175,15 @@ int potts_create_ex(int32_t L, int32_t q, int32_t start, uint64_t seed,
   int rc = POTTS_OK;
   do {
     cudaError_t e = cudaGetDevice(&h->device);
-    if (e != cudaSuccess) { rc = fail(POTTS_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e)); break; }
+    if (e != cudaSuccess) {
+      rc = fail(POTTS_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+      break;
+    }
     e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) { rc = fail(POTTS_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)); break; }
+    if (e != cudaSuccess) {
+      rc = fail(POTTS_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+      break;
+    }
     h->stream = h->own_stream;
     e = cudaMalloc(&h->d_planes, (size_t)(2 * h->plane_bytes));
     if (e != cudaSuccess) {
@@ -190,12 +196,24 @@ int potts_create_ex(int32_t L, int32_t q, int32_t start, uint64_t seed,
     h->rec_cap = std::max<int64_t>(1, kRecordBytesTarget / ((1 + q) * 8));
     const size_t rec_bytes = (size_t)h->rec_cap * (1 + q) * 8;
     e = cudaMalloc(&h->d_rec, rec_bytes);
-    if (e != cudaSuccess) { cudaGetLastError(); h->d_rec = nullptr; rc = fail(POTTS_ENOMEM, "cudaMalloc records: %s", cudaGetErrorString(e)); break; }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      h->d_rec = nullptr;
+      rc = fail(POTTS_ENOMEM, "cudaMalloc records: %s", cudaGetErrorString(e));
+      break;
+    }
     e = cudaMallocHost(&h->h_rec, rec_bytes);
-    if (e != cudaSuccess) { cudaGetLastError(); h->h_rec = nullptr; rc = fail(POTTS_ENOMEM, "cudaMallocHost records: %s", cudaGetErrorString(e)); break; }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      h->h_rec = nullptr;
+      rc = fail(POTTS_ENOMEM, "cudaMallocHost records: %s",
+                cudaGetErrorString(e));
+      break;
+    }
     h->geom = choose_geom(L, h->H, q, sm_count_of_current_device(), 0);
     if (start == POTTS_START_ORDERED) {
-      e = cudaMemsetAsync(h->d_planes, 0, (size_t)(2 * h->plane_bytes), h->stream);
+      e = cudaMemsetAsync(h->d_planes, 0, (size_t)(2 * h->plane_bytes),
+                          h->stream);
     } else {
       const int64_t sites = (int64_t)L * (L / 2);
       e = launch_init_random(h->d_planes, sites, (uint32_t)q, 0, seed,
@@ -205,7 +223,10 @@ int potts_create_ex(int32_t L, int32_t q, int32_t start, uint64_t seed,
                                (uint32_t)q, 1, seed, (uint32_t)layout,
                                h->stream);
     }
-    if (e != cudaSuccess) { rc = fail(POTTS_ECUDA, "init: %s", cudaGetErrorString(e)); break; }
+    if (e != cudaSuccess) {
+      rc = fail(POTTS_ECUDA, "init: %s", cudaGetErrorString(e));
+      break;
+    }
     rc = recount_into_obs(h);
   } while (0);
   if (rc != POTTS_OK) {

@@ -1,12 +1,13 @@
 // Serving loop: continuous batching of simulation requests on one GPU.
 //
 // A host thread owns an Engine.  Each iteration it (1) admits queued
-// requests (oldest first, or smallest work first), while a slot is free and the device bytes in use
-// plus the request's planes fit the budget, allocating and initialising
-// their lattices; (2) drops cancelled requests; (3) runs one batched step of
-// up to sweeps_per_step sweeps over every active lattice; (4) appends each
-// lattice's new per-sweep records to its request's outbox and retires the
-// lattices that are done, freeing their slot and memory.  Clients talk to
+// requests (oldest first, or smallest work first) while a slot is free and
+// the device bytes in use plus the request's planes fit the budget,
+// allocating and initialising their lattices; (2) drops cancelled
+// requests; (3) runs one batched step of up to sweeps_per_step sweeps over
+// every active lattice; (4) appends each lattice's new per-sweep records to
+// its request's outbox and retires the lattices that are done, freeing
+// their slot and memory.  Clients talk to
 // the loop only through the mutex-protected queue and outboxes
 // (potts_serve_submit / poll / cancel), which never block on the GPU.
 #include <algorithm>
