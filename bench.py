@@ -657,26 +657,6 @@ def run_reference(args):
     }
 
 
-def run_rng_ceiling():
-    """Builds and runs paper_1101_0876_gb300/diag/rng_ceiling.cu (the
-    random-number work of the sweep alone) and prints its JSON line."""
-    src = os.path.join(ROOT, "paper_1101_0876_gb300", "diag", "rng_ceiling.cu")
-    out_dir = os.path.join(ROOT, "paper_1101_0876_gb300", "_build")
-    os.makedirs(out_dir, exist_ok=True)
-    exe = os.path.join(out_dir, "rng_ceiling")
-    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a",
-                    "-O3", "-std=c++17", "-o", exe, src], check=True)
-    r = subprocess.run([exe], capture_output=True, text=True, check=True)
-    line = json.loads(r.stdout.strip().splitlines()[-1])
-    hbm, _ = measured_peaks()
-    full = hbm * 1e9 / 3.0
-    line["hbm_roofline_sites_per_s"] = full
-    line["philox_frac_of_hbm_roofline"] = line["philox_sites_per_s"] / full
-    line["proposal_frac_of_hbm_roofline"] = (
-        line["philox_proposal_sites_per_s"] / full)
-    print(json.dumps(line), flush=True)
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -704,12 +684,7 @@ def main():
     ap.add_argument("--served-rate", type=float, default=200.0,
                     help="Poisson arrival rate of the served stream (req/s)")
     ap.add_argument("--served-k", type=int, default=32)
-    ap.add_argument("--rng-ceiling", action="store_true",
-                    help="time the random-number work alone and exit")
     args = ap.parse_args()
-    if args.rng_ceiling:
-        run_rng_ceiling()
-        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
