@@ -98,6 +98,12 @@ def lib() -> ctypes.CDLL:
             ctypes.c_uint64, ctypes.c_double, ctypes.c_int64, i64p, u8p,
             ctypes.c_int32]
         L.oracle_sweep_sites_ex.restype = ctypes.c_int
+        L.oracle_band_pass.argtypes = [u8p, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_uint64, ctypes.c_uint64,
+                                       ctypes.c_int32, ctypes.c_double,
+                                       ctypes.c_int32, u64p]
+        L.oracle_band_pass.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -185,6 +191,23 @@ def init_sites(L: int, q: int, start: int, seed: int,
     if rc != 0:
         raise ValueError("oracle_init_sites: bad arguments")
     return out
+
+
+def band_pass(rows: np.ndarray, L: int, q: int, r0: int, seed: int,
+              sweep: int, colour: int, beta: float, partial: np.ndarray,
+              update: int = METROPOLIS) -> None:
+    """One colour pass over the band held in `rows` ((n + 2) x L bytes, the
+    first and last rows being the rows just above and below the band; the
+    band is global rows r0 .. r0 + n - 1), updated in place; the band's
+    partial record {B (black pass), hist} is added to `partial`."""
+    assert rows.dtype == np.uint8 and rows.flags.c_contiguous
+    assert rows.shape[1] == L and rows.shape[0] >= 3
+    assert partial.dtype == np.uint64 and partial.size == 1 + q
+    rc = lib().oracle_band_pass(_ptr(rows, ctypes.c_uint8), rows.shape[0] - 2,
+                                L, q, r0, seed, sweep, colour, float(beta),
+                                int(update), _ptr(partial, ctypes.c_uint64))
+    if rc != 0:
+        raise ValueError("oracle_band_pass: bad arguments")
 
 
 class Lattice:

@@ -480,3 +480,38 @@ int oracle_sweep_sites_ex(const uint8_t *pre, int32_t L, int32_t q,
   }
   return 0;
 }
+
+/* ---------------------------------------------------------------------
+ * A band of rows (row-strip decomposition, Sec. 7): the colour pass of the
+ * sweep restricted to rows r0 .. r0 + n - 1, with the rows just above and
+ * below supplied by the caller.  Same rule, same words, same raster order
+ * as oracle_sweep_ex within the band.
+ * ------------------------------------------------------------------- */
+int oracle_band_pass(uint8_t *rows, int32_t n, int32_t L, int32_t q,
+                     int32_t r0, uint64_t seed, uint64_t t, int32_t c,
+                     double beta, int32_t update, uint64_t *partial) {
+  update_rule ur;
+  if ((L & 1) != 0 || L < 4 || q < 2 || q > 256 || n < 1 || r0 < 0 ||
+      r0 + n > L || (c != 0 && c != 1))
+    return -1;
+  if (rule_setup(&ur, update, beta, q) != 0) return -1;
+  for (int32_t r = 1; r <= n; ++r) {
+    const int32_t gi = r0 + r - 1;
+    for (int32_t j = 0; j < L; ++j) {
+      if (((gi + j) & 1) != c) continue;
+      int nb[4], dB;
+      nb[0] = rows[(int64_t)(r - 1) * L + j];
+      nb[1] = rows[(int64_t)(r + 1) * L + j];
+      nb[2] = rows[(int64_t)r * L + wrap(j - 1, L)];
+      nb[3] = rows[(int64_t)r * L + wrap(j + 1, L)];
+      uint32_t u = oracle_site_word(seed, t, (uint32_t)c,
+                                    colour_index(L, gi, j));
+      int now = apply_rule(&ur, rows[(int64_t)r * L + j], nb, u, q, &dB);
+      rows[(int64_t)r * L + j] = (uint8_t)now;
+      partial[1 + now] += 1;
+      if (c == 1)
+        for (int m = 0; m < 4; ++m) partial[0] += (uint64_t)(nb[m] == now);
+    }
+  }
+  return 0;
+}

@@ -98,6 +98,23 @@ int oracle_sweep_sites_ex(const uint8_t *pre, int32_t L, int32_t q,
                           int64_t nsites, const int64_t *idx, uint8_t *out,
                           int32_t update);
 
+/* One colour pass over a band of rows of an L x L lattice, for the row-strip
+ * decomposition of one lattice over several devices (the multi-GPU extension
+ * Sec. 7 proposes).  rows: (n + 2) x L row-major bytes: row 0 holds global
+ * row r0 - 1 (mod L), rows 1..n hold global rows r0 .. r0 + n - 1, row n + 1
+ * holds global row r0 + n (mod L).  Every site of colour c in rows 1..n takes
+ * one step of the update rule (update: 0 Metropolis, 1 heat bath) of sweep t,
+ * in raster order, against its neighbours as they stand in `rows` (columns
+ * periodic), with the random word of its global colour index.  partial
+ * (1 + q words) is added to: partial[1 + v] += updated sites now in state v;
+ * for c = 1 also partial[0] += neighbours equal to each updated site after
+ * its step (every bond has exactly one black end, so over all bands the
+ * black pass counts B).  L even, n >= 1, 0 <= r0, r0 + n <= L.  Returns 0,
+ * or -1 for bad arguments. */
+int oracle_band_pass(uint8_t *rows, int32_t n, int32_t L, int32_t q,
+                     int32_t r0, uint64_t seed, uint64_t t, int32_t c,
+                     double beta, int32_t update, uint64_t *partial);
+
 #ifdef __cplusplus
 }
 #endif
