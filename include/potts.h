@@ -49,7 +49,8 @@
  *     device before returning.
  *   - Version 200 (0.2.0) added the heat-bath rule (potts_set_update,
  *     potts_heatbath_weights, potts_batch_set_update, potts_req.update);
- *     version 210 the fused sweep (potts_set_schedule).
+ *     version 210 the fused sweep (potts_set_schedule); version 220 row
+ *     strips (potts_create_sharded, potts_strip_*).
  */
 #ifndef POTTS_H
 #define POTTS_H
@@ -200,10 +201,11 @@ int potts_device_planes(potts_h h, void **white, void **black,
 int potts_destroy(potts_h h);
 
 /* Sweeps a lattice held in caller-owned device memory without allocating
- * anything (the paper has no counterpart: it exists for callers that cannot
- * allocate device memory when they sweep, e.g. code running during CUDA
- * graph capture, or inside a framework whose caching allocator already
- * holds the device memory).
+ * anything.  The paper has no counterpart: this exists for callers that
+ * must not allocate device memory at the point where they sweep, such as
+ * code inside a framework whose caching allocator has already reserved the
+ * device memory, or loops that cannot afford the device-wide
+ * synchronisation an allocation may cause.
  * white, black: device pointers (16-byte aligned) to the two colour planes
  *   in the POTTS_LAYOUT_U8 layout (L rows x L/2 bytes each, row i of the
  *   white plane holding the sites (i, j) with i + j even in order of j);
@@ -211,19 +213,86 @@ int potts_destroy(potts_h h);
  * sweep: global index of the first sweep; seed, beta as for potts_sweep.
  * out_counts: NULL, or host or device memory for nsweeps * (1 + q) uint64
  *   records {B, hist[0..q-1]}.
- * stream: a cudaStream_t or NULL (legacy default stream); the call returns
- *   after the work on it has finished.
+ * stream: a cudaStream_t or NULL (legacy default stream).  The call
+ *   synchronises this stream before it returns.
  * Limit: nsweeps * (1 + q) <= 8192 per call (the records accumulate in a
  *   fixed 64 KiB device array that every device loading the library holds
- *   until exit); larger requests fail with POTTS_EINVAL.  All calls on a
- *   device share that array, so calls that overlap on the GPU (different
- *   streams or threads) race; serialise them.  The first call on a device
- *   looks up the array's device address; make that first call before any
- *   stream capture.  Results equal potts_sweep's bit for bit. */
+ *   until exit); larger requests fail with POTTS_EINVAL.
+ * Sharing: every call on a device uses that one array.  Calls that
+ *   overlapped on the GPU would race on it and could return POTTS_OK with
+ *   wrong records, so the library serialises its own calls per device with
+ *   a host lock held from the first launch until the stream has
+ *   synchronised; calls from several host threads therefore queue.
+ * Set-up: the first call on a device looks up the array's device address
+ *   and keeps it for the life of the process.  After cudaDeviceReset (or
+ *   anything else that destroys the device's primary context) that address
+ *   is stale: do not call this entry point on that device again.
+ * Results equal potts_sweep's bit for bit. */
 int potts_sweep_planes_noalloc(void *white, void *black, int32_t L, int32_t q,
                                uint64_t seed, uint64_t sweep, double beta,
                                int64_t nsweeps, uint64_t *out_counts,
                                void *stream);
+
+/* ------------------------------------------------------------- row strips
+ * One lattice split into bands of rows (the multi-GPU extension Sec. 7
+ * proposes, on the colour-packed planes of Sec. 3.3).  A strip owns lattice
+ * rows [row0, row0 + nrows) of both colour planes and keeps a copy of the
+ * row just above and the row just below its band (halo rows, periodic).
+ * Before the pass of colour c every strip needs fresh halo rows of plane
+ * 1 - c; after the black pass the strips' partial records {B, hist} sum to
+ * the lattice's record (every bond has exactly one black end).  Random words
+ * are keyed by the global site index, so any split gives the single-lattice
+ * result bit for bit. */
+
+/* A lattice split into nstrips strips held by this process: strip s has an
+ * even number of rows (as equal as possible, strip 0 first) and lives on
+ * device devices[s] (NULL: all on the current device).  The handle works
+ * with potts_sweep, potts_observables, potts_reset_averages,
+ * potts_get_spins, potts_set_state, potts_set_update and potts_destroy,
+ * with the same results as potts_create_ex(L, q, start, seed, layout);
+ * halo rows move by device-to-device copies ordered by events, one stream
+ * per strip.  Not available on it: potts_set_stream, potts_device_planes,
+ * the fused schedule.  Errors: EINVAL (arguments as for potts_create_ex;
+ * nstrips outside [1, L/2]; a device index out of range), ENOMEM, ECUDA. */
+int potts_create_sharded(int32_t L, int32_t q, int32_t start, uint64_t seed,
+                         int32_t layout, int32_t nstrips,
+                         const int32_t *devices, potts_h *out);
+
+/* One strip of an L x L lattice on the current device, for callers that
+ * hold one strip per process and move the halo rows themselves (e.g. NCCL
+ * send/receive between neighbouring ranks).  row0 and nrows even,
+ * nrows >= 2, row0 + nrows <= L.  Its own rows start as the lattice's would
+ * (ordered or random start); halo rows start at 0.  Works with potts_destroy,
+ * potts_set_stream, potts_set_update, potts_device_planes (planes of
+ * nrows + 2 rows, halo rows included) and, on its own rows (nrows x L
+ * row-major bytes), potts_get_spins and potts_set_state (no counts are kept
+ * for a strip; set_state sets the strip's sweep index).  potts_sweep
+ * rejects it: it sweeps with potts_strip_pass.  Errors: EINVAL, ENOMEM,
+ * ECUDA. */
+int potts_strip_create(int32_t L, int32_t q, int32_t start, uint64_t seed,
+                       int32_t layout, int32_t row0, int32_t nrows,
+                       potts_h *out);
+
+/* Device addresses of four rows of the strip's plane `colour` (0 white, 1
+ * black), each *row_bytes long: rows[0] its first own row, rows[1] its last
+ * own row (what the neighbours above and below need), rows[2] the halo row
+ * above, rows[3] the halo row below (where the neighbours' rows go).  Owned
+ * by the handle. */
+int potts_strip_rows(potts_h h, int32_t colour, void **rows,
+                     int64_t *row_bytes);
+
+/* The pass of colour `colour` of the strip's current sweep over its own
+ * rows, queued on the strip's stream.  The halo rows of plane 1 - colour
+ * must hold the neighbours' rows as they stand after the neighbours' latest
+ * pass of colour 1 - colour.  d_record: device memory of 1 + q uint64 the
+ * strip's partial counts are added to (the histogram of its updated sites,
+ * and on the black pass the satisfied bonds of its black sites); the caller
+ * zeroes it per sweep and sums it over the strips.  Passes alternate white
+ * (0), black (1); the black pass advances the strip's sweep index.  Does
+ * not synchronise.  Errors: EINVAL (not a strip, colour, beta as for
+ * potts_sweep), ECUDA. */
+int potts_strip_pass(potts_h h, double beta, int32_t colour,
+                     uint64_t *d_record);
 
 /* ------------------------------------------------------------------ batch
  * n independent lattices (the paper's "several samples", Sec. 3) swept

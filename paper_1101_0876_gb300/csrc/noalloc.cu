@@ -1,14 +1,14 @@
 // Sweep entry point that allocates no memory.
 //
-// Who needs it: callers that cannot call cudaMalloc (or anything that does)
-// at the point where they want to sweep, for example code that runs while a
-// CUDA graph is being captured (allocation is not allowed there), code that
-// runs inside another framework whose caching allocator already reserved
-// the device memory, or real-time loops where an allocation's implicit
-// device synchronisation would stall other work.  They own the two colour
-// planes and the output buffer; the only extra memory this path needs is
-// the per-sweep record accumulator, which here is a fixed file-scope device
-// array instead of a cudaMalloc'd buffer.
+// Who needs it: callers that must not call cudaMalloc (or anything that
+// does) at the point where they sweep: code running inside another
+// framework whose caching allocator has already reserved the device memory
+// for itself, or loops that cannot afford the implicit device-wide
+// synchronisation an allocation may cause.  They own the two colour planes
+// and the output buffer; the only extra memory this path needs is the
+// per-sweep record accumulator, which here is a fixed file-scope device
+// array instead of a cudaMalloc'd buffer.  The call synchronises its stream
+// before it returns.
 #include <mutex>
 
 #include "internal.cuh"
@@ -25,15 +25,14 @@ __device__ __align__(256) unsigned long long g_noalloc_records[kNoAllocRecordWor
 constexpr int kMaxDevices = 64;
 unsigned long long *g_records_addr[kMaxDevices] = {};
 std::mutex g_setup_mu;
+// One lock per device, held from the first launch of a call until its
+// stream has synchronised: calls from several host threads on one device
+// then run one after the other instead of racing on the shared array.
+std::mutex g_call_mu[kMaxDevices];
 
 // Device address of the accumulator on the current device, looked up once
 // per device (the host-side symbol is only a stand-in for it).
-int records_address(unsigned long long **out) {
-  int dev = 0;
-  POTTS_CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices)
-    return potts::fail(POTTS_EINVAL, "device %d is beyond the %d supported",
-                       dev, kMaxDevices);
+int records_address(int dev, unsigned long long **out) {
   std::lock_guard<std::mutex> lk(g_setup_mu);
   if (!g_records_addr[dev]) {
     void *p = nullptr;
@@ -70,10 +69,16 @@ extern "C" int potts_sweep_planes_noalloc(void *white, void *black, int32_t L,
   uint64_t thr[5];
   if (!threshold_table(beta, thr))
     return fail(POTTS_EINVAL, "beta must be finite and >= 0 (got %g)", beta);
+  int dev = 0;
+  POTTS_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices)
+    return fail(POTTS_EINVAL, "device %d is beyond the %d supported", dev,
+                kMaxDevices);
   unsigned long long *rec = nullptr;
-  int rc = records_address(&rec);
+  int rc = records_address(dev, &rec);
   if (rc) return rc;
   if (nsweeps == 0) return POTTS_OK;
+  std::lock_guard<std::mutex> serialise(g_call_mu[dev]);
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const AcceptTable T = accept_table(thr);
@@ -96,20 +101,32 @@ extern "C" int potts_sweep_planes_noalloc(void *white, void *black, int32_t L,
     A[c].one = 1u;
     A[c].hist_bins = 256u;
     A[c].layout = kLayoutU8;
+    A[c].grow0 = 0;
+    A[c].row_lo = 0;
+    A[c].row_end = L;
   }
   // the accumulator keeps the previous call's contents: clear what is used
-  POTTS_CK(cudaMemsetAsync(rec, 0, (size_t)words * 8, st));
-  for (int64_t s = 0; s < nsweeps; ++s) {
-    const uint64_t t = sweep + (uint64_t)s;
-    for (int c = 0; c < 2; ++c) {
-      A[c].t_lo = (uint32_t)t;
-      A[c].t_hi = (uint32_t)(t >> 32);
-      POTTS_CK(launch_pass(A[c], T, G, rec + s * (1 + q), st));
+  rc = [&]() -> int {
+    POTTS_CK(cudaMemsetAsync(rec, 0, (size_t)words * 8, st));
+    for (int64_t s = 0; s < nsweeps; ++s) {
+      const uint64_t t = sweep + (uint64_t)s;
+      for (int c = 0; c < 2; ++c) {
+        A[c].t_lo = (uint32_t)t;
+        A[c].t_hi = (uint32_t)(t >> 32);
+        POTTS_CK(launch_pass(A[c], T, G, rec + s * (1 + q), st));
+      }
     }
-  }
-  if (out_counts)
-    POTTS_CK(cudaMemcpyAsync(out_counts, rec, (size_t)words * 8,
-                             cudaMemcpyDefault, st));
-  POTTS_CK(cudaStreamSynchronize(st));
+    if (out_counts)
+      POTTS_CK(cudaMemcpyAsync(out_counts, rec, (size_t)words * 8,
+                               cudaMemcpyDefault, st));
+    return POTTS_OK;
+  }();
+  // also after a failed launch: whatever was queued finishes before the
+  // lock lets another call touch the array
+  const cudaError_t es = cudaStreamSynchronize(st);
+  if (rc) return rc;
+  if (es != cudaSuccess)
+    return fail(POTTS_ECUDA, "cudaStreamSynchronize: %s",
+                cudaGetErrorString(es));
   return POTTS_OK;
 }

@@ -1,16 +1,21 @@
 """The entry point that allocates nothing (potts_sweep_planes_noalloc).
 
-It serves callers that cannot allocate device memory when they sweep (code
-running during CUDA graph capture, or inside a framework whose allocator
-already holds the memory): they own the planes and the output, and the
-library accumulates records in a fixed device array.  Its results must
-equal the allocating entry point's bit for bit, call after call.  This file
-is collected last so that a stop at the first failure has run every other
-test; it also passes alone in a fresh process.
+It serves callers that must not allocate device memory where they sweep
+(code inside a framework whose caching allocator already holds the device
+memory, or loops that cannot afford the synchronisation an allocation may
+cause): they own the planes and the output, and the library accumulates the
+records in one fixed device array.  Its results must equal the CPU oracle's
+and the allocating entry point's bit for bit, call after call, whether the
+records go to host memory, to device memory or nowhere.  This file is
+collected last so that a stop at the first failure has run every other test;
+it also passes alone in a fresh process.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
+import oracle
 from paper_1101_0876_gb300 import potts, workloads
 
 pytestmark = pytest.mark.gpu
@@ -38,30 +43,56 @@ def _from_planes(white, black):
     return s
 
 
+def _call(dw, db, L, q, seed, t, beta, n, out_ptr, stream):
+    """One call through the C ABI; out_ptr: host or device address, or None."""
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    out = ctypes.cast(ctypes.c_void_p(out_ptr), u64p) if out_ptr else None
+    rc = potts.lib().potts_sweep_planes_noalloc(
+        ctypes.c_void_p(dw.data_ptr()), ctypes.c_void_p(db.data_ptr()), L, q,
+        seed, t, beta, n, out, ctypes.c_void_p(stream))
+    assert rc == 0, potts.last_error()
+
+
 @pytest.mark.parametrize("L,q,use_torch_stream", [(256, 9, False),
                                                   (544, 24, True)])
-def test_noalloc_equals_allocating_path(L, q, use_torch_stream):
+def test_noalloc_equals_oracle_and_allocating_path(L, q, use_torch_stream):
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     from paper_1101_0876_gb300 import build
     build.build()
     seed, beta = 21, workloads.beta_at(q, 1.0)
-    ref = potts.Lattice(L, q, potts.START_RANDOM, seed)
-    w, b = _to_planes(ref.spins())
+    ora = oracle.Lattice(L, q, 1, seed)           # the CPU reference
+    ref = potts.Lattice(L, q, potts.START_RANDOM, seed)   # allocating path
+    start = ora.spins()
+    assert np.array_equal(ref.spins(), start)
+    w, b = _to_planes(start)
     dw = torch.from_numpy(w).cuda()
     db = torch.from_numpy(b).cuda()
     stream = torch.cuda.Stream() if use_torch_stream else None
-    handle = stream.cuda_stream if stream is not None else None
+    handle = stream.cuda_stream if stream is not None else 0
     torch.cuda.synchronize()
     t = 0
-    for n in (7, 5):              # two calls in a row share the fixed buffer
-        got = potts.sweep_planes_noalloc(dw.data_ptr(), db.data_ptr(), L, q,
-                                         seed, t, beta, n, stream=handle)
-        want = ref.sweep(beta, n)
-        assert np.array_equal(got, want), n
+    # two calls in a row with records in host memory
+    for n in (7, 5):
+        host = np.zeros((n, 1 + q), dtype=np.uint64)
+        _call(dw, db, L, q, seed, t, beta, n, host.ctypes.data, handle)
+        assert np.array_equal(host, ora.sweep(beta, n)), (t, n)
+        assert np.array_equal(host, ref.sweep(beta, n)), (t, n)
         t += n
+    # no records at all
+    _call(dw, db, L, q, seed, t, beta, 3, None, handle)
+    ora.sweep(beta, 3, records=False)
+    ref.sweep(beta, 3, records=False)
+    t += 3
+    # records into device memory
+    dev = torch.zeros((4, 1 + q), dtype=torch.int64, device="cuda")
+    _call(dw, db, L, q, seed, t, beta, 4, dev.data_ptr(), handle)
+    got = dev.cpu().numpy().view(np.uint64)
+    assert np.array_equal(got, ora.sweep(beta, 4))
+    assert np.array_equal(got, ref.sweep(beta, 4))
     spins = _from_planes(dw.cpu().numpy(), db.cpu().numpy())
+    assert np.array_equal(spins, ora.spins())
     assert np.array_equal(spins, ref.spins())
 
 
