@@ -105,6 +105,9 @@ __global__ void __launch_bounds__(kPassThreads,
   A.one = 1u;
   A.hist_bins = q;
   A.layout = kLayoutU8;
+  A.grow0 = 0;  // whole lattices
+  A.row_lo = 0;
+  A.row_end = d.L;
   const PhiloxKey ks = philox_schedule(A.key0, A.key1);
   const int32_t item = (bid - d.tile0) * kPassThreads + (int32_t)tid;
   const int32_t rg = item / d.nchunks;
@@ -586,7 +589,7 @@ int Engine::drain() {
 }
 
 int Engine::copy_spins(const Member *m, uint8_t *out_LxL) {
-  return download_rowmajor(m->planes, m->planes + m->plane_bytes, m->L,
+  return download_rowmajor(m->planes, m->planes + m->plane_bytes, m->L, m->L,
                            kLayoutU8, out_LxL, st_);
 }
 

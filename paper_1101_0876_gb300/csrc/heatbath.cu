@@ -47,9 +47,9 @@ __global__ void __launch_bounds__(kPassThreads, QB <= 6 ? 4 : POTTS_HB_MINB)
   uint32_t ne = 0, rows_done = 0;
   if (rg < G.RG && chunk * 16 < A.H) {
     for (int32_t tile = blockIdx.y; tile < G.ty; tile += gridDim.y) {
-      const int32_t i0 = (tile * G.RG + rg) * G.TR;
-      if (i0 >= A.L) continue;
-      const int32_t rows = min(G.TR, A.L - i0);
+      const int32_t i0 = A.row_lo + (tile * G.RG + rg) * G.TR;
+      if (i0 >= A.row_end) continue;
+      const int32_t rows = min(G.TR, A.row_end - i0);
       hb_walk_column<QB, COLOUR, COUNTS, PAIRS, LAY>(
           A, ks, s_W, T.m, chunk * 16, i0, rows,
           hist ? s_hist + (tid & 31u) : nullptr, &ne);

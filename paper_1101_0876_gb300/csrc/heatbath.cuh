@@ -245,7 +245,7 @@ __device__ __forceinline__ void hb_row(const PassArgs &A, const PhiloxKey &ks,
     Wd[2] = __funnelshift_r(Cw[2], Cw[3], 8);
     Wd[3] = __funnelshift_r(Cw[3], ew, 8);
   }
-  const uint32_t g0 = (uint32_t)(((int64_t)w.i * H + x0) >> 2);
+  const uint32_t g0 = (uint32_t)(((int64_t)(w.i + A.grow0) * H + x0) >> 2);
   uint32_t Nw[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -314,7 +314,7 @@ __device__ __forceinline__ void hb_walk_column(
   w.i = i0;
   uint32_t ne_acc = 0;
   int32_t r = 0;
-  if ((i0 & 1) == 0) {
+  if (((i0 + A.grow0) & 1) == 0) {
     for (; r + 2 <= rows; r += 2) {
       hb_row<QB, COLOUR == 0, COUNTS, PAIRS, LAY>(
           A, ks, sW, m, w, x0, xb, xl, xr, RB, true, lane_hist, ne_acc);
@@ -328,7 +328,7 @@ __device__ __forceinline__ void hb_walk_column(
     }
   }
   for (; r < rows; ++r) {
-    const bool left = ((w.i + COLOUR) & 1) == 0;
+    const bool left = ((w.i + A.grow0 + COLOUR) & 1) == 0;
     if (left)
       hb_row<QB, true, COUNTS, PAIRS, LAY>(A, ks, sW, m, w, x0, xb, xl, xr,
                                            RB, r + 1 < rows, lane_hist, ne_acc);

@@ -125,14 +125,25 @@ cudaError_t launch_pass_hb(const PassArgs &A, const HeatTable &T,
                            const TileGeom &G, unsigned long long *rec,
                            cudaStream_t st);
 // Random start of one plane of plane_sites sites: s = floor(u q / 2^32),
-// u = Philox word of domain 2 + colour at sweep 0.
+// u = Philox word of domain 2 + colour at sweep 0.  site0: colour-class
+// index of the plane's first site (a multiple of 16; 0 for a whole
+// lattice).
 cudaError_t launch_init_random(uint8_t *plane, int64_t plane_sites,
                                uint32_t q, uint32_t colour, uint64_t seed,
-                               uint32_t layout, cudaStream_t st);
+                               uint32_t layout, cudaStream_t st,
+                               int64_t site0 = 0);
 // Recount {B, hist} from the planes into rec (must start at zero).
 cudaError_t launch_recount(const uint8_t *white, const uint8_t *black,
                            int32_t L, int32_t H, uint32_t q, uint32_t layout,
                            unsigned long long *rec, cudaStream_t st);
+// The same over rows [row_lo, row_lo + nrows) of planes of Lp rows (row
+// indices periodic in Lp) whose row 0 is lattice row grow0: the bonds of
+// those rows' black sites and the states of their sites.
+cudaError_t launch_recount_rows(const uint8_t *white, const uint8_t *black,
+                                int32_t Lp, int32_t H, int32_t row_lo,
+                                int32_t nrows, int32_t grow0, uint32_t q,
+                                uint32_t layout, unsigned long long *rec,
+                                cudaStream_t st);
 
 // Both colour passes of one Metropolis sweep in one launch (fused.cu):
 // U8 layout, L a multiple of 1024.  Reads the planes (white, black), writes
@@ -155,10 +166,13 @@ void update_obs(potts_obs *obs, const uint64_t *rec, int32_t L, int32_t q,
 // planes (layout.cu), through a device staging buffer and conversion
 // kernels on stream st; both synchronise st.  upload_rowmajor writes the
 // planes only if every spin is < q (else POTTS_EINVAL).  Return POTTS_*.
+// nrows: rows of the block (L for a whole lattice; a row strip's own rows,
+// starting at an even lattice row, with white/black at its first row).
 int download_rowmajor(const uint8_t *white, const uint8_t *black, int32_t L,
-                      uint32_t layout, uint8_t *out_LxL, cudaStream_t st);
-int upload_rowmajor(const uint8_t *in_LxL, int32_t L, uint32_t q,
-                    uint32_t layout, uint8_t *white, uint8_t *black,
-                    cudaStream_t st);
+                      int32_t nrows, uint32_t layout, uint8_t *out_LxL,
+                      cudaStream_t st);
+int upload_rowmajor(const uint8_t *in_LxL, int32_t L, int32_t nrows,
+                    uint32_t q, uint32_t layout, uint8_t *white,
+                    uint8_t *black, cudaStream_t st);
 
 }  // namespace potts

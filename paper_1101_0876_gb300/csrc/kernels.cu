@@ -46,9 +46,9 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_PASS_MINB)
   uint32_t ne = 0, rows_done = 0;
   if (rg < G.RG && chunk * 16 < A.H) {
     for (int32_t tile = blockIdx.y; tile < G.ty; tile += gridDim.y) {
-      const int32_t i0 = (tile * G.RG + rg) * G.TR;
-      if (i0 >= A.L) continue;
-      const int32_t rows = min(G.TR, A.L - i0);
+      const int32_t i0 = A.row_lo + (tile * G.RG + rg) * G.TR;
+      if (i0 >= A.row_end) continue;
+      const int32_t rows = min(G.TR, A.row_end - i0);
       walk_column<QB, COLOUR, COUNTS, PAIRS, LT0, LAY>(
           A, ks, reinterpret_cast<const uint8_t *>(s_tab), chunk * 16, i0,
           rows, hist ? s_hist + (tid & 31u) : nullptr, &ne);
@@ -198,16 +198,20 @@ TileGeom choose_geom(int32_t L, int32_t H, int32_t q, int32_t sm_count,
 // -------------------------------------------------------- random start
 // One thread per 16 sites of a plane (site index = byte index for U8):
 // s = floor(u q / 2^32), u = Philox word of domain 2 + colour at sweep 0.
+// site0: index within the colour class of the plane's first site (0 for a
+// whole lattice, r0 * L / 2 for a row strip starting at lattice row r0).
 __global__ void init_random_kernel(uint8_t *plane, int64_t nchunks,
                                    uint32_t q, uint32_t domain, uint32_t key0,
-                                   uint32_t key1, uint32_t layout) {
+                                   uint32_t key1, uint32_t layout,
+                                   uint32_t ctr0) {
   const PhiloxKey ks = philox_schedule(key0, key1);
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks;
        c += (int64_t)gridDim.x * blockDim.x) {
     uint32_t w[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const uint4 u = philox10((uint32_t)(c * 4 + j), 0u, domain, 0u, ks);
+      const uint4 u =
+          philox10(ctr0 + (uint32_t)(c * 4 + j), 0u, domain, 0u, ks);
       const uint32_t p0 = (uint32_t)(((uint64_t)u.x * q) >> 32);
       const uint32_t p1 = (uint32_t)(((uint64_t)u.y * q) >> 32);
       const uint32_t p2 = (uint32_t)(((uint64_t)u.z * q) >> 32);
@@ -224,24 +228,29 @@ __global__ void init_random_kernel(uint8_t *plane, int64_t nchunks,
 
 cudaError_t launch_init_random(uint8_t *plane, int64_t plane_sites,
                                uint32_t q, uint32_t colour, uint64_t seed,
-                               uint32_t layout, cudaStream_t st) {
+                               uint32_t layout, cudaStream_t st,
+                               int64_t site0) {
+  if (plane_sites % 16 || site0 % 16) return cudaErrorInvalidValue;
   const int64_t nchunks = plane_sites / 16;
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((nchunks + threads - 1) / threads,
                                            (int64_t)1 << 20);
   init_random_kernel<<<(unsigned)blocks, threads, 0, st>>>(
       plane, nchunks, q, 2u + colour, (uint32_t)seed, (uint32_t)(seed >> 32),
-      layout);
+      layout, (uint32_t)(site0 >> 2));
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ recount
 // One thread per 16-byte chunk of a black row: satisfied bonds of the 16
 // black sites with their four white neighbours, and the states of those
-// black sites and of the white sites at the same (i, x).
+// black sites and of the white sites at the same (i, x).  Rows
+// [row_lo, row_lo + nrows) of planes with Lp rows (periodic in Lp) whose
+// row 0 is lattice row grow0.
 template <int LAY>
 __global__ void recount_kernel(const uint8_t *white, const uint8_t *black,
-                               int32_t L, int32_t H, uint32_t q,
+                               int32_t Lp, int32_t H, int32_t row_lo,
+                               int32_t nrows, int32_t grow0, uint32_t q,
                                unsigned long long *rec) {
   using IO = Lay<LAY>;
   extern __shared__ uint32_t s_hist[];
@@ -250,21 +259,22 @@ __global__ void recount_kernel(const uint8_t *white, const uint8_t *black,
   for (uint32_t v = tid; v < q * 32u; v += blockDim.x) s_hist[v] = 0;
   if (tid == 0) s_sat = 0;
   __syncthreads();
-  const int64_t nch = (int64_t)L * (H / 16);
+  const int64_t nch = (int64_t)nrows * (H / 16);
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + tid;
   const int32_t RB = IO::row_bytes(H);
   uint32_t sat = 0;
   if (c < nch) {
-    const int32_t i = (int32_t)(c / (H / 16));
+    const int32_t i = row_lo + (int32_t)(c / (H / 16));
     const int32_t x0 = (int32_t)(c % (H / 16)) * 16;
     const int32_t xb = LAY == kLayoutU4 ? x0 / 2 : x0;
-    const int32_t im = i == 0 ? L - 1 : i - 1, ip = i + 1 == L ? 0 : i + 1;
+    const int32_t im = i == 0 ? Lp - 1 : i - 1, ip = i + 1 == Lp ? 0 : i + 1;
     uint32_t Uw[4], Dw[4], Cw[4], Sw[4];
     IO::load(white + (int64_t)im * RB + xb, false, Uw);
     IO::load(white + (int64_t)ip * RB + xb, false, Dw);
     IO::load(white + (int64_t)i * RB + xb, false, Cw);
     IO::load(black + (int64_t)i * RB + xb, false, Sw);
-    const bool left = ((i + 1) & 1) == 0;  // black: x-1 when i+1 even
+    // black: x-1 when lattice row + 1 is even
+    const bool left = ((i + grow0 + 1) & 1) == 0;
     const int32_t xe = left ? (x0 == 0 ? RB - 4 : xb - 4)
                             : (x0 + 16 == H ? 0 : xb + IO::kChunkBytes);
     const uint32_t ew = IO::edge(
@@ -302,16 +312,24 @@ __global__ void recount_kernel(const uint8_t *white, const uint8_t *black,
 cudaError_t launch_recount(const uint8_t *white, const uint8_t *black,
                            int32_t L, int32_t H, uint32_t q, uint32_t layout,
                            unsigned long long *rec, cudaStream_t st) {
-  const int64_t nch = (int64_t)L * (H / 16);
+  return launch_recount_rows(white, black, L, H, 0, L, 0, q, layout, rec, st);
+}
+
+cudaError_t launch_recount_rows(const uint8_t *white, const uint8_t *black,
+                                int32_t Lp, int32_t H, int32_t row_lo,
+                                int32_t nrows, int32_t grow0, uint32_t q,
+                                uint32_t layout, unsigned long long *rec,
+                                cudaStream_t st) {
+  const int64_t nch = (int64_t)nrows * (H / 16);
   const int threads = 256;
   const int64_t blocks = (nch + threads - 1) / threads;
   const size_t smem = (size_t)q * 32u * 4u;
   if (layout == kLayoutU4)
     recount_kernel<kLayoutU4><<<(unsigned)blocks, threads, smem, st>>>(
-        white, black, L, H, q, rec);
+        white, black, Lp, H, row_lo, nrows, grow0, q, rec);
   else
     recount_kernel<kLayoutU8><<<(unsigned)blocks, threads, smem, st>>>(
-        white, black, L, H, q, rec);
+        white, black, Lp, H, row_lo, nrows, grow0, q, rec);
   return cudaGetLastError();
 }
 

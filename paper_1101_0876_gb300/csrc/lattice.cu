@@ -6,7 +6,7 @@
 #include <new>
 
 #include "heatbath.cuh"
-#include "internal.cuh"
+#include "lattice.cuh"
 
 namespace potts {
 
@@ -92,29 +92,9 @@ void update_obs(potts_obs *obs, const uint64_t *rec, int32_t L, int32_t q,
 
 using namespace potts;
 
-struct potts_lattice {
-  int32_t L = 0, q = 0, layout = POTTS_LAYOUT_U8;
-  int32_t H = 0;            // bytes per plane row
-  uint64_t seed = 0;
-  uint64_t sweep = 0;       // next global sweep index
-  int device = 0;
-  uint8_t *d_planes = nullptr;  // white plane then black plane
-  uint8_t *d_alt = nullptr;     // second pair the fused sweep writes into
-  int64_t plane_bytes = 0;
-  cudaStream_t own_stream = nullptr;
-  cudaStream_t stream = nullptr;
-  unsigned long long *d_rec = nullptr;  // [rec_cap][1+q]
-  uint64_t *h_rec = nullptr;            // pinned copy
-  int64_t rec_cap = 0;
-  TileGeom geom{};
-  potts_obs obs{};
-  int32_t update = POTTS_UPDATE_METROPOLIS;
-  int32_t schedule = POTTS_SCHEDULE_TWO_PASS;
-};
+namespace potts {
 
-static constexpr int64_t kRecordBytesTarget = 4 << 20;
-
-static int recount_into_obs(potts_h h) {
+int recount_into_obs(potts_h h) {
   const int32_t q = h->q;
   POTTS_CK(cudaMemsetAsync(h->d_rec, 0, (size_t)(1 + q) * 8, h->stream));
   POTTS_CK(launch_recount(h->d_planes, h->d_planes + h->plane_bytes, h->L,
@@ -127,8 +107,18 @@ static int recount_into_obs(potts_h h) {
   return POTTS_OK;
 }
 
-static void free_lattice(potts_h h) {
+void free_lattice(potts_h h) {
   if (!h) return;
+  for (size_t i = 0; i < h->parts.size(); ++i) {
+    potts_h part = h->parts[i];
+    if (!part) continue;
+    DeviceScope device_scope(part->device);
+    if (part->stream) cudaStreamSynchronize(part->stream);
+    for (int c = 0; c < 2; ++c)
+      if (2 * i + c < h->pass_done.size() && h->pass_done[2 * i + c])
+        cudaEventDestroy(h->pass_done[2 * i + c]);
+    free_lattice(part);
+  }
   if (h->d_planes) cudaFree(h->d_planes);
   if (h->d_alt) cudaFree(h->d_alt);
   if (h->d_rec) cudaFree(h->d_rec);
@@ -137,11 +127,13 @@ static void free_lattice(potts_h h) {
   delete h;
 }
 
+}  // namespace potts
+
 extern "C" {
 
 const char *potts_last_error(void) { return g_err.c_str(); }
 
-int potts_version(void) { return 210; }
+int potts_version(void) { return 220; }
 
 int potts_threshold_table(double beta, uint64_t out_thr[5]) {
   if (!out_thr) return fail(POTTS_EINVAL, "out_thr is NULL");
@@ -245,6 +237,10 @@ int potts_create(int32_t L, int32_t q, int32_t start, uint64_t seed,
 
 int potts_sweep(potts_h h, double beta, int64_t nsweeps, uint64_t *out_counts) {
   if (!h) return fail(POTTS_EINVAL, "handle is NULL");
+  if (!h->parts.empty()) return sharded_sweep(h, beta, nsweeps, out_counts);
+  if (h->strip)
+    return fail(POTTS_EINVAL,
+                "a row-strip handle sweeps through potts_strip_pass");
   DeviceScope device_scope(h->device);
   if (nsweeps < 0) return fail(POTTS_EINVAL, "nsweeps < 0");
   uint64_t thr[5];
@@ -277,6 +273,9 @@ int potts_sweep(potts_h h, double beta, int64_t nsweeps, uint64_t *out_counts) {
     A[c].one = 1u;
     A[c].hist_bins = (uint32_t)q;
     A[c].layout = (uint32_t)h->layout;
+    A[c].grow0 = 0;
+    A[c].row_lo = 0;
+    A[c].row_end = h->L;
   }
   int64_t done = 0;
   while (done < nsweeps) {
@@ -324,6 +323,7 @@ int potts_set_update(potts_h h, int32_t update) {
   if (update != POTTS_UPDATE_METROPOLIS && update != POTTS_UPDATE_HEATBATH)
     return fail(POTTS_EINVAL, "unknown update rule %d", update);
   h->update = update;
+  for (potts_h part : h->parts) part->update = update;
   return POTTS_OK;
 }
 
@@ -331,6 +331,8 @@ int potts_set_schedule(potts_h h, int32_t schedule) {
   if (!h) return fail(POTTS_EINVAL, "handle is NULL");
   if (schedule != POTTS_SCHEDULE_TWO_PASS && schedule != POTTS_SCHEDULE_FUSED)
     return fail(POTTS_EINVAL, "unknown sweep schedule %d", schedule);
+  if (schedule == POTTS_SCHEDULE_FUSED && (h->strip || !h->parts.empty()))
+    return fail(POTTS_EINVAL, "row strips sweep with two colour passes");
   if (schedule == POTTS_SCHEDULE_FUSED &&
       !fused_supported(h->L, h->q, h->layout))
     return fail(POTTS_EINVAL,
@@ -365,15 +367,32 @@ int potts_reset_averages(potts_h h) {
 
 int potts_get_spins(potts_h h, uint8_t *out_LxL) {
   if (!h || !out_LxL) return fail(POTTS_EINVAL, "NULL argument");
+  if (!h->parts.empty()) return sharded_get_spins(h, out_LxL);
   DeviceScope device_scope(h->device);
+  if (h->strip)  // the strip's own rows
+    return download_rowmajor(h->d_planes + h->row_bytes,
+                             h->d_planes + h->plane_bytes + h->row_bytes,
+                             h->L, h->nrows, (uint32_t)h->layout, out_LxL,
+                             h->stream);
   return download_rowmajor(h->d_planes, h->d_planes + h->plane_bytes, h->L,
-                           (uint32_t)h->layout, out_LxL, h->stream);
+                           h->L, (uint32_t)h->layout, out_LxL, h->stream);
 }
 
 int potts_set_state(potts_h h, const uint8_t *LxL, uint64_t sweep) {
   if (!h || !LxL) return fail(POTTS_EINVAL, "NULL argument");
+  if (!h->parts.empty()) return sharded_set_state(h, LxL, sweep);
   DeviceScope device_scope(h->device);
-  const int rc = upload_rowmajor(LxL, h->L, (uint32_t)h->q,
+  if (h->strip) {  // the strip's own rows; no counts are kept for a strip
+    const int rc = upload_rowmajor(
+        LxL, h->L, h->nrows, (uint32_t)h->q, (uint32_t)h->layout,
+        h->d_planes + h->row_bytes, h->d_planes + h->plane_bytes + h->row_bytes,
+        h->stream);
+    if (rc) return rc;
+    h->sweep = sweep;
+    h->obs.sweep = sweep;
+    return POTTS_OK;
+  }
+  const int rc = upload_rowmajor(LxL, h->L, h->L, (uint32_t)h->q,
                                  (uint32_t)h->layout, h->d_planes,
                                  h->d_planes + h->plane_bytes, h->stream);
   if (rc) return rc;
@@ -384,6 +403,9 @@ int potts_set_state(potts_h h, const uint8_t *LxL, uint64_t sweep) {
 
 int potts_set_stream(potts_h h, void *stream) {
   if (!h) return fail(POTTS_EINVAL, "handle is NULL");
+  if (!h->parts.empty())
+    return fail(POTTS_EINVAL, "a lattice split into row strips runs one "
+                "stream per strip");
   // finish work queued on the old stream before switching
   POTTS_CK(cudaStreamSynchronize(h->stream));
   h->stream = stream ? (cudaStream_t)stream : h->own_stream;
@@ -393,6 +415,9 @@ int potts_set_stream(potts_h h, void *stream) {
 int potts_device_planes(potts_h h, void **white, void **black,
                         int64_t *row_bytes, int32_t *layout) {
   if (!h) return fail(POTTS_EINVAL, "handle is NULL");
+  if (!h->parts.empty())
+    return fail(POTTS_EINVAL, "a lattice split into row strips has no single "
+                "pair of planes");
   if (white) *white = h->d_planes;
   if (black) *black = h->d_planes + h->plane_bytes;
   if (row_bytes)

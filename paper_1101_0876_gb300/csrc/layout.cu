@@ -8,7 +8,9 @@
 // Row i of the row-major lattice holds, at column j = 2x + p, the site that
 // sits at byte x of row i of the plane of colour (i + p) % 2: even rows
 // interleave (white, black), odd rows (black, white).  A thread converts 32
-// row-major bytes, i.e. 16 sites of each plane.
+// row-major bytes, i.e. 16 sites of each plane.  The conversions work on a
+// block of nrows rows that starts at an even lattice row (the whole lattice,
+// or the rows a row strip owns).
 #include <algorithm>
 
 #include "internal.cuh"
@@ -42,10 +44,11 @@ __global__ void check_spins_kernel(const uint8_t *in, int64_t n, uint32_t q,
 
 template <int LAY>
 __global__ void rowmajor_to_planes_kernel(const uint8_t *in, int32_t L,
-                                          uint8_t *white, uint8_t *black) {
+                                          int32_t nrows, uint8_t *white,
+                                          uint8_t *black) {
   const int32_t H = L / 2, nch = H / 16;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)L * nch) return;
+  if (t >= (int64_t)nrows * nch) return;
   const int32_t i = (int32_t)(t / nch), c = (int32_t)(t - (int64_t)i * nch);
   const uint4 *src = reinterpret_cast<const uint4 *>(in + (int64_t)i * L) +
                      2 * c;
@@ -77,10 +80,10 @@ __global__ void rowmajor_to_planes_kernel(const uint8_t *in, int32_t L,
 template <int LAY>
 __global__ void planes_to_rowmajor_kernel(const uint8_t *white,
                                           const uint8_t *black, int32_t L,
-                                          uint8_t *out) {
+                                          int32_t nrows, uint8_t *out) {
   const int32_t H = L / 2, nch = H / 16;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)L * nch) return;
+  if (t >= (int64_t)nrows * nch) return;
   const int32_t i = (int32_t)(t / nch), c = (int32_t)(t - (int64_t)i * nch);
   uint32_t W[4], B[4];
   if constexpr (LAY == kLayoutU4) {
@@ -128,45 +131,48 @@ cudaError_t launch_check_spins(const uint8_t *in, int64_t n, uint32_t q,
 }
 
 cudaError_t launch_rowmajor_to_planes(const uint8_t *in, int32_t L,
-                                      uint32_t layout, uint8_t *white,
-                                      uint8_t *black, cudaStream_t st) {
+                                      int32_t nrows, uint32_t layout,
+                                      uint8_t *white, uint8_t *black,
+                                      cudaStream_t st) {
   if (L % 32) return cudaErrorInvalidValue;
-  const unsigned grid = grid_for((int64_t)L * (L / 32));
+  const unsigned grid = grid_for((int64_t)nrows * (L / 32));
   if (layout == kLayoutU4)
     rowmajor_to_planes_kernel<kLayoutU4>
-        <<<grid, kLayoutThreads, 0, st>>>(in, L, white, black);
+        <<<grid, kLayoutThreads, 0, st>>>(in, L, nrows, white, black);
   else
     rowmajor_to_planes_kernel<kLayoutU8>
-        <<<grid, kLayoutThreads, 0, st>>>(in, L, white, black);
+        <<<grid, kLayoutThreads, 0, st>>>(in, L, nrows, white, black);
   return cudaGetLastError();
 }
 
 cudaError_t launch_planes_to_rowmajor(const uint8_t *white,
                                       const uint8_t *black, int32_t L,
-                                      uint32_t layout, uint8_t *out,
-                                      cudaStream_t st) {
+                                      int32_t nrows, uint32_t layout,
+                                      uint8_t *out, cudaStream_t st) {
   if (L % 32) return cudaErrorInvalidValue;
-  const unsigned grid = grid_for((int64_t)L * (L / 32));
+  const unsigned grid = grid_for((int64_t)nrows * (L / 32));
   if (layout == kLayoutU4)
     planes_to_rowmajor_kernel<kLayoutU4>
-        <<<grid, kLayoutThreads, 0, st>>>(white, black, L, out);
+        <<<grid, kLayoutThreads, 0, st>>>(white, black, L, nrows, out);
   else
     planes_to_rowmajor_kernel<kLayoutU8>
-        <<<grid, kLayoutThreads, 0, st>>>(white, black, L, out);
+        <<<grid, kLayoutThreads, 0, st>>>(white, black, L, nrows, out);
   return cudaGetLastError();
 }
 
 // Device staging buffer of n bytes on the stream's memory pool, copy of the
 // planes in row-major order, copy to the caller's host buffer.
 int download_rowmajor(const uint8_t *white, const uint8_t *black, int32_t L,
-                      uint32_t layout, uint8_t *out_LxL, cudaStream_t st) {
-  const size_t n = (size_t)L * (size_t)L;
+                      int32_t nrows, uint32_t layout, uint8_t *out_LxL,
+                      cudaStream_t st) {
+  const size_t n = (size_t)nrows * (size_t)L;
   uint8_t *stage = nullptr;
   if (cudaMallocAsync(&stage, n, st) != cudaSuccess) {
     cudaGetLastError();
     return fail(POTTS_ENOMEM, "device staging buffer of %zu bytes", n);
   }
-  cudaError_t e = launch_planes_to_rowmajor(white, black, L, layout, stage, st);
+  cudaError_t e =
+      launch_planes_to_rowmajor(white, black, L, nrows, layout, stage, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out_LxL, stage, n, cudaMemcpyDeviceToHost, st);
   const cudaError_t ef = cudaFreeAsync(stage, st);
@@ -180,10 +186,10 @@ int download_rowmajor(const uint8_t *white, const uint8_t *black, int32_t L,
 // Copy of the caller's row-major spins to a device staging buffer, range
 // check (every spin < q), then the split into the planes.  The planes are
 // written only when every spin is in range.
-int upload_rowmajor(const uint8_t *in_LxL, int32_t L, uint32_t q,
-                    uint32_t layout, uint8_t *white, uint8_t *black,
-                    cudaStream_t st) {
-  const size_t n = (size_t)L * (size_t)L;
+int upload_rowmajor(const uint8_t *in_LxL, int32_t L, int32_t nrows,
+                    uint32_t q, uint32_t layout, uint8_t *white,
+                    uint8_t *black, cudaStream_t st) {
+  const size_t n = (size_t)nrows * (size_t)L;
   uint8_t *stage = nullptr;
   if (cudaMallocAsync(&stage, n + 256, st) != cudaSuccess) {
     cudaGetLastError();
@@ -199,7 +205,7 @@ int upload_rowmajor(const uint8_t *in_LxL, int32_t L, uint32_t q,
     e = cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess && bad == ~0ull)
-    e = launch_rowmajor_to_planes(stage, L, layout, white, black, st);
+    e = launch_rowmajor_to_planes(stage, L, nrows, layout, white, black, st);
   const cudaError_t ef = cudaFreeAsync(stage, st);
   if (e == cudaSuccess) e = ef;
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -45,6 +45,15 @@ struct PassArgs {
   uint32_t hist_bins;    // shared histogram bins: q, or 256 when the planes
                          // come from the caller unchecked (any byte value
                          // then indexes inside the histogram)
+  // Rows of the planes and their place in the lattice.  A whole lattice:
+  // L rows, grow0 = 0, rows [0, L) updated, row indices periodic in L.  A
+  // row strip of one lattice (rows r0 .. r0 + n - 1 of it): L = n + 2 rows,
+  // row 0 and row n + 1 holding copies of the rows just above and below the
+  // strip, grow0 = r0 - 1 (the lattice row of plane row 0), rows [1, n + 1)
+  // updated; no row index wraps then.  The random-number counters and the
+  // checkerboard parity use the lattice row grow0 + i.
+  int32_t grow0;
+  int32_t row_lo, row_end;
 };
 
 // Bytes of the shared acceptance table: entry k (dE + 4) at offset 16 k,
@@ -306,7 +315,7 @@ __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
     Wd[2] = __funnelshift_r(Cw[2], Cw[3], 8);
     Wd[3] = __funnelshift_r(Cw[3], ew, 8);
   }
-  const uint32_t g0 = (uint32_t)(((int64_t)w.i * H + x0) >> 2);
+  const uint32_t g0 = (uint32_t)(((int64_t)(w.i + A.grow0) * H + x0) >> 2);
   uint32_t Nw[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -380,9 +389,10 @@ __device__ __forceinline__ void walk_column(const PassArgs &A,
   w.i = i0;
   uint32_t ne_acc = 0;
   int32_t r = 0;
-  // Side neighbour at x-1 when (i + colour) is even.  Walks start on even
-  // rows when rows is even, so pairs of rows have a fixed pattern.
-  if ((i0 & 1) == 0) {
+  // Side neighbour at x-1 when (lattice row + colour) is even.  Walks start
+  // on even lattice rows when rows is even, so pairs of rows have a fixed
+  // pattern.
+  if (((i0 + A.grow0) & 1) == 0) {
     for (; r + 2 <= rows; r += 2) {
       do_row<QB, COLOUR == 0, COUNTS, PAIRS, LT0, LAY>(
           A, ks, tab, w, x0, xb, xl, xr, RB, true, lane_hist, ne_acc);
@@ -395,7 +405,7 @@ __device__ __forceinline__ void walk_column(const PassArgs &A,
     }
   }
   for (; r < rows; ++r) {
-    const bool left = ((w.i + COLOUR) & 1) == 0;
+    const bool left = ((w.i + A.grow0 + COLOUR) & 1) == 0;
     if (left)
       do_row<QB, true, COUNTS, PAIRS, LT0, LAY>(
           A, ks, tab, w, x0, xb, xl, xr, RB, r + 1 < rows, lane_hist, ne_acc);

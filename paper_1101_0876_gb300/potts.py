@@ -103,6 +103,19 @@ _SIGS = {
         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
         ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int64,
         _u64p, ctypes.c_void_p]),
+    "potts_create_sharded": (ctypes.c_int, [
+        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+        ctypes.c_int32, ctypes.c_int32, _i32p,
+        ctypes.POINTER(ctypes.c_void_p)]),
+    "potts_strip_create": (ctypes.c_int, [
+        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+        ctypes.POINTER(ctypes.c_void_p)]),
+    "potts_strip_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_void_p),
+                                        _i64p]),
+    "potts_strip_pass": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double,
+                                        ctypes.c_int32, ctypes.c_void_p]),
     "potts_batch_create": (ctypes.c_int, [ctypes.c_int32, _i32p, _i32p,
                                           _i32p, _u64p,
                                           ctypes.POINTER(ctypes.c_void_p)]),
@@ -206,11 +219,26 @@ class Lattice:
     """One L x L lattice with q states resident on the current GPU."""
 
     def __init__(self, L: int, q: int, start: int = START_ORDERED,
-                 seed: int = 0, layout: int = LAYOUT_AUTO):
+                 seed: int = 0, layout: int = LAYOUT_AUTO,
+                 nstrips: int = 0, devices=None):
+        """nstrips > 0: the lattice split into that many row strips
+        (potts_create_sharded), strip s on devices[s] (default: the current
+        device for all)."""
         self.L, self.q, self.seed = int(L), int(q), int(seed)
         h = ctypes.c_void_p()
-        check(lib().potts_create_ex(self.L, self.q, int(start), self.seed,
-                                    int(layout), ctypes.byref(h)))
+        if nstrips:
+            dev = None
+            if devices is not None:
+                devs = np.ascontiguousarray(devices, dtype=np.int32)
+                assert devs.size == int(nstrips)
+                dev = _ptr(devs, ctypes.c_int32)
+            check(lib().potts_create_sharded(
+                self.L, self.q, int(start), self.seed, int(layout),
+                int(nstrips), dev, ctypes.byref(h)))
+        else:
+            check(lib().potts_create_ex(self.L, self.q, int(start),
+                                        self.seed, int(layout),
+                                        ctypes.byref(h)))
         self._h = h
 
     def close(self):
@@ -295,6 +323,71 @@ class Lattice:
     @property
     def sweep_index(self) -> int:
         return int(self.observables()["sweep"])
+
+
+class Strip:
+    """One row strip of an L x L lattice on the current GPU: lattice rows
+    [row0, row0 + nrows) of both colour planes plus one halo row above and
+    below (potts_strip_create).  The caller moves the halo rows between
+    strips (rows()) and sums the partial records of the strips."""
+
+    def __init__(self, L: int, q: int, start: int, seed: int, row0: int,
+                 nrows: int, layout: int = LAYOUT_AUTO):
+        self.L, self.q, self.seed = int(L), int(q), int(seed)
+        self.row0, self.nrows = int(row0), int(nrows)
+        h = ctypes.c_void_p()
+        check(lib().potts_strip_create(self.L, self.q, int(start), self.seed,
+                                       int(layout), self.row0, self.nrows,
+                                       ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            check(lib().potts_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rows(self, colour: int):
+        """(first own, last own, halo above, halo below) device addresses of
+        plane `colour`, and the bytes per row."""
+        arr = (ctypes.c_void_p * 4)()
+        rb = ctypes.c_int64()
+        check(lib().potts_strip_rows(self._h, int(colour), arr,
+                                     ctypes.byref(rb)))
+        return tuple(int(a or 0) for a in arr), int(rb.value)
+
+    def pass_(self, beta: float, colour: int, d_record: int) -> None:
+        """Queues the colour pass on the strip's stream; its partial counts
+        are added to the 1 + q uint64 at device address d_record."""
+        check(lib().potts_strip_pass(self._h, float(beta), int(colour),
+                                     ctypes.c_void_p(d_record)))
+
+    def set_stream(self, stream_handle: int | None) -> None:
+        check(lib().potts_set_stream(self._h, ctypes.c_void_p(
+            stream_handle or None)))
+
+    def set_update(self, update: int) -> None:
+        check(lib().potts_set_update(self._h, int(update)))
+
+    def spins(self, out: np.ndarray | None = None) -> np.ndarray:
+        """The strip's own rows, nrows x L row-major."""
+        if out is None:
+            out = np.empty((self.nrows, self.L), dtype=np.uint8)
+        assert out.dtype == np.uint8 and out.flags.c_contiguous
+        assert out.size == self.nrows * self.L
+        check(lib().potts_get_spins(self._h, _ptr(out, ctypes.c_uint8)))
+        return out
+
+    def set_state(self, rows: np.ndarray, sweep: int) -> None:
+        s = np.ascontiguousarray(rows, dtype=np.uint8)
+        assert s.shape == (self.nrows, self.L)
+        check(lib().potts_set_state(self._h, _ptr(s, ctypes.c_uint8),
+                                    int(sweep)))
 
 
 class Batch:
