@@ -55,6 +55,8 @@ struct TileGeom {
   int32_t CX, RG, TR;
   int32_t gx, gy, ty;
   int32_t pairs;  // histogram bins are (state, state) pairs (q <= 16)
+  int32_t sites;  // sites per thread and row: 16, or 32 (U8 Metropolis)
+  int32_t nibble; // 1: the U4 Metropolis pass on nibbles (pass_u4.cuh)
 };
 constexpr int kPassThreads = 128;
 
@@ -64,8 +66,16 @@ constexpr int kPassThreads = 128;
 #define POTTS_PASS_MINB 6
 #endif
 
+// L: rows to cover; chunk: sites per thread and row (16 or 32); minb: the
+// kernel's resident CTAs per SM.
 TileGeom choose_geom(int32_t L, int32_t H, int32_t q, int32_t sm_count,
-                     int32_t tr_hint);
+                     int32_t tr_hint, int32_t chunk = 16,
+                     int32_t minb = POTTS_PASS_MINB);
+// The shape of the colour pass launch_pass / launch_pass_hb will run for
+// nrows rows of width H: the U4 Metropolis pass on nibbles, the U8
+// Metropolis pass with 32 sites per thread where H allows, else 16.
+TileGeom pass_geom(int32_t nrows, int32_t H, int32_t q, int32_t layout,
+                   int32_t update, int32_t sm_count);
 
 // Programmatic dependent launch.  A colour pass is launched so that it may
 // start while the previous kernel on its stream finishes: its CTAs clear

@@ -1,9 +1,11 @@
 // Kernels of the single-lattice path: the colour pass (white pass, and the
 // black pass fused with the per-sweep counts), the random start and a full
-// recount.  The per-thread work is in pass_u8.cuh.
+// recount.  The per-thread work is in pass_u8.cuh (byte words) and
+// pass_u4.cuh (nibble words, the packed 4-bit layout).
 #include <algorithm>
 
 #include "internal.cuh"
+#include "pass_u4.cuh"
 
 namespace potts {
 
@@ -18,8 +20,15 @@ namespace potts {
 // non-empty bin per CTA, without a second kernel or a CPU-side sum).
 constexpr int kPairBins = 256;
 
-template <int QB, int COLOUR, bool PAIRS, bool LT0, int LAY>
-__global__ void __launch_bounds__(kPassThreads, POTTS_PASS_MINB)
+// Resident CTAs per SM the pass kernels are compiled for: 128 threads x
+// 80 registers for 16 sites per thread, 168 for 32 (where the longer rows
+// save per-row work: 1.208 against 1.241 ps per update at L = 32768), and
+// 128 for the nibble pass.
+constexpr int kMinb32 = 3, kMinbNib = 4;
+
+template <int QB, int COLOUR, bool PAIRS, bool LT0, int LAY, int NW>
+__global__ void __launch_bounds__(kPassThreads,
+                                  NW == 8 ? kMinb32 : POTTS_PASS_MINB)
     pass_kernel(PassArgs A, AcceptTable Tin, TileGeom G,
                 unsigned long long *rec) {
   constexpr bool COUNTS = COLOUR == 1;
@@ -44,13 +53,13 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_PASS_MINB)
   const int32_t cx = (int32_t)tid % G.CX, rg = (int32_t)tid / G.CX;
   const int32_t chunk = (int32_t)blockIdx.x * G.CX + cx;
   uint32_t ne = 0, rows_done = 0;
-  if (rg < G.RG && chunk * 16 < A.H) {
+  if (rg < G.RG && chunk * 4 * NW < A.H) {
     for (int32_t tile = blockIdx.y; tile < G.ty; tile += gridDim.y) {
       const int32_t i0 = A.row_lo + (tile * G.RG + rg) * G.TR;
       if (i0 >= A.row_end) continue;
       const int32_t rows = min(G.TR, A.row_end - i0);
-      walk_column<QB, COLOUR, COUNTS, PAIRS, LT0, LAY>(
-          A, ks, reinterpret_cast<const uint8_t *>(s_tab), chunk * 16, i0,
+      walk_column<QB, COLOUR, COUNTS, PAIRS, LT0, LAY, NW>(
+          A, ks, reinterpret_cast<const uint8_t *>(s_tab), chunk * 4 * NW, i0,
           rows, hist ? s_hist + (tid & 31u) : nullptr, &ne);
       rows_done += (uint32_t)rows;
     }
@@ -58,7 +67,7 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_PASS_MINB)
   pdl_release_next();
   if (!hist) return;
   if (COUNTS) {
-    uint32_t sat = 64u * rows_done - ne;
+    uint32_t sat = 16u * NW * rows_done - ne;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sat += __shfl_xor_sync(0xFFFFFFFFu, sat, o);
     if ((tid & 31u) == 0 && sat) atomicAdd(&s_sat, sat);
@@ -89,7 +98,66 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_PASS_MINB)
   }
 }
 
-template <int QB, int COLOUR, bool PAIRS, int LAY = kLayoutU8>
+// The U4 Metropolis pass on nibble words (pass_u4.cuh): 16 sites per thread
+// and row, pair bins (every byte of a nibble word is a pair of sites).
+template <int COLOUR, bool LT0>
+__global__ void __launch_bounds__(kPassThreads, kMinbNib)
+    pass_u4_kernel(PassArgs A, AcceptTable Tin, TileGeom G,
+                   unsigned long long *rec) {
+  constexpr bool COUNTS = COLOUR == 1;
+  extern __shared__ uint32_t s_hist[];  // 256 pair bins * 32 lanes
+  __shared__ __align__(16) uint32_t s_tab[kTabWords];
+  __shared__ uint32_t s_sat;
+  __shared__ uint32_t s_fold[16];
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t i = tid; i < (uint32_t)kTabWords; i += kPassThreads)
+    s_tab[i] = (i % 4u == 0 && i / 4u < 9u) ? Tin.tab[i / 4u] : 0u;
+  for (uint32_t v = tid; v < (uint32_t)kPairBins * 32u; v += kPassThreads)
+    s_hist[v] = 0;
+  if (tid < 16) s_fold[tid] = 0;
+  if (tid == 0) s_sat = 0;
+  __syncthreads();
+  pdl_wait_previous();
+
+  const PhiloxKey ks = philox_schedule(A.key0, A.key1);
+  const int32_t cx = (int32_t)tid % G.CX, rg = (int32_t)tid / G.CX;
+  const int32_t chunk = (int32_t)blockIdx.x * G.CX + cx;
+  uint32_t ne = 0, rows_done = 0;
+  if (rg < G.RG && chunk * 16 < A.H) {
+    for (int32_t tile = blockIdx.y; tile < G.ty; tile += gridDim.y) {
+      const int32_t i0 = A.row_lo + (tile * G.RG + rg) * G.TR;
+      if (i0 >= A.row_end) continue;
+      const int32_t rows = min(G.TR, A.row_end - i0);
+      nib_walk_column<COLOUR, COUNTS, LT0>(
+          A, ks, reinterpret_cast<const uint8_t *>(s_tab), chunk * 16, i0,
+          rows, s_hist + (tid & 31u), &ne);
+      rows_done += (uint32_t)rows;
+    }
+  }
+  pdl_release_next();
+  if (COUNTS) {
+    uint32_t sat = 64u * rows_done - ne;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sat += __shfl_xor_sync(0xFFFFFFFFu, sat, o);
+    if ((tid & 31u) == 0 && sat) atomicAdd(&s_sat, sat);
+  }
+  __syncthreads();
+  if (COUNTS && tid == 0 && s_sat) atomicAdd(rec, (unsigned long long)s_sat);
+  for (uint32_t p = tid; p < (uint32_t)kPairBins; p += kPassThreads) {
+    uint32_t sum = 0;
+#pragma unroll 8
+    for (int l = 0; l < 32; ++l) sum += s_hist[p * 32u + l];
+    if (sum) {
+      atomicAdd(&s_fold[p & 15u], sum);
+      atomicAdd(&s_fold[p >> 4], sum);
+    }
+  }
+  __syncthreads();
+  if (tid < A.q && s_fold[tid])
+    atomicAdd(rec + 1 + tid, (unsigned long long)s_fold[tid]);
+}
+
+template <int QB, int COLOUR, bool PAIRS, int LAY = kLayoutU8, int NW = 4>
 static cudaError_t launch_c(const PassArgs &A, const AcceptTable &T,
                             const TileGeom &G, unsigned long long *rec,
                             cudaStream_t st) {
@@ -98,24 +166,20 @@ static cudaError_t launch_c(const PassArgs &A, const AcceptTable &T,
       rec ? (size_t)(PAIRS ? kPairBins : A.hist_bins) * 32u * sizeof(uint32_t)
           : 0;
   if (T.rule_lt0)
-    return launch_pdl(pass_kernel<QB, COLOUR, PAIRS, true, LAY>, grid, block,
-                      smem, st, A, T, G, rec);
-  return launch_pdl(pass_kernel<QB, COLOUR, PAIRS, false, LAY>, grid, block,
-                    smem, st, A, T, G, rec);
+    return launch_pdl(pass_kernel<QB, COLOUR, PAIRS, true, LAY, NW>, grid,
+                      block, smem, st, A, T, G, rec);
+  return launch_pdl(pass_kernel<QB, COLOUR, PAIRS, false, LAY, NW>, grid,
+                    block, smem, st, A, T, G, rec);
 }
 
 template <int QB>
 static cudaError_t launch_qb(const PassArgs &A, const AcceptTable &T,
                              const TileGeom &G, unsigned long long *rec,
                              cudaStream_t st) {
+  if (G.sites == 32)
+    return A.colour ? launch_c<QB, 1, false, kLayoutU8, 8>(A, T, G, rec, st)
+                    : launch_c<QB, 0, false, kLayoutU8, 8>(A, T, G, rec, st);
   if constexpr (QB == 4) {
-    if (A.layout == kLayoutU4) {
-      if (G.pairs)
-        return A.colour ? launch_c<QB, 1, true, kLayoutU4>(A, T, G, rec, st)
-                        : launch_c<QB, 0, true, kLayoutU4>(A, T, G, rec, st);
-      return A.colour ? launch_c<QB, 1, false, kLayoutU4>(A, T, G, rec, st)
-                      : launch_c<QB, 0, false, kLayoutU4>(A, T, G, rec, st);
-    }
     if (G.pairs)
       return A.colour ? launch_c<QB, 1, true>(A, T, G, rec, st)
                       : launch_c<QB, 0, true>(A, T, G, rec, st);
@@ -124,10 +188,31 @@ static cudaError_t launch_qb(const PassArgs &A, const AcceptTable &T,
                   : launch_c<QB, 0, false>(A, T, G, rec, st);
 }
 
+static cudaError_t launch_u4(const PassArgs &A, const AcceptTable &T,
+                             const TileGeom &G, unsigned long long *rec,
+                             cudaStream_t st) {
+  dim3 grid(G.gx, G.gy), block(kPassThreads);
+  const size_t smem = (size_t)kPairBins * 32u * sizeof(uint32_t);
+  if (T.rule_lt0)
+    return A.colour ? launch_pdl(pass_u4_kernel<1, true>, grid, block, smem,
+                                 st, A, T, G, rec)
+                    : launch_pdl(pass_u4_kernel<0, true>, grid, block, smem,
+                                 st, A, T, G, rec);
+  return A.colour ? launch_pdl(pass_u4_kernel<1, false>, grid, block, smem, st,
+                               A, T, G, rec)
+                  : launch_pdl(pass_u4_kernel<0, false>, grid, block, smem, st,
+                               A, T, G, rec);
+}
+
 cudaError_t launch_pass(const PassArgs &A, const AcceptTable &T,
                         const TileGeom &G, unsigned long long *rec,
                         cudaStream_t st) {
-  if (A.layout == kLayoutU4 && A.q > 16) return cudaErrorInvalidValue;
+  if (A.layout == kLayoutU4) {
+    // the nibble pass always histograms into its pair bins
+    if (A.q > 16 || !G.nibble || !rec) return cudaErrorInvalidValue;
+    return launch_u4(A, T, G, rec, st);
+  }
+  if (G.nibble || (G.sites == 32 && A.H % 32)) return cudaErrorInvalidValue;
   switch (qbits_for((int32_t)A.q)) {
     case 4: return launch_qb<4>(A, T, G, rec, st);
     case 5: return launch_qb<5>(A, T, G, rec, st);
@@ -146,13 +231,15 @@ int qbits_for(int32_t q) {
 }
 
 TileGeom choose_geom(int32_t L, int32_t H, int32_t q, int32_t sm_count,
-                     int32_t tr_hint) {
+                     int32_t tr_hint, int32_t chunk, int32_t minb) {
   TileGeom g;
-  const int32_t nchunks = H / 16;
+  g.sites = chunk;
+  g.nibble = 0;
+  const int32_t nchunks = H / chunk;
   g.CX = std::min(nchunks, kPassThreads);
   g.RG = kPassThreads / g.CX;
   g.gx = (nchunks + g.CX - 1) / g.CX;
-  const int64_t max_ctas = (int64_t)std::max(sm_count, 1) * POTTS_PASS_MINB;
+  const int64_t max_ctas = (int64_t)std::max(sm_count, 1) * minb;
   // Longest walk (<= 32 rows) that still gives every resident CTA about
   // four row tiles, so that the tiles balance across CTAs.
   int32_t tr = 1;
@@ -193,6 +280,26 @@ TileGeom choose_geom(int32_t L, int32_t H, int32_t q, int32_t sm_count,
   const int64_t sites_per_cta = (int64_t)L * H / ((int64_t)g.gx * g.gy);
   g.pairs = (q <= 16 && sites_per_cta >= 65536) ? 1 : 0;
   return g;
+}
+
+TileGeom pass_geom(int32_t nrows, int32_t H, int32_t q, int32_t layout,
+                   int32_t update, int32_t sm_count) {
+  if (update == POTTS_UPDATE_HEATBATH)
+    return choose_geom(nrows, H, q, sm_count, 0);
+  if (layout == kLayoutU4) {
+    TileGeom g = choose_geom(nrows, H, q, sm_count, 0, 16, kMinbNib);
+    g.pairs = 1;
+    g.nibble = 1;
+    return g;
+  }
+  if (H % 32 == 0) {
+    // one state per bin: with 32 sites per thread the pair bins' 32 KB of
+    // shared memory per CTA buy nothing (1.2102 against 1.2076 ps)
+    TileGeom g = choose_geom(nrows, H, q, sm_count, 0, 32, kMinb32);
+    g.pairs = 0;
+    return g;
+  }
+  return choose_geom(nrows, H, q, sm_count, 0);
 }
 
 // -------------------------------------------------------- random start

@@ -202,7 +202,7 @@ int potts_create_ex(int32_t L, int32_t q, int32_t start, uint64_t seed,
                 cudaGetErrorString(e));
       break;
     }
-    h->geom = choose_geom(L, h->H, q, sm_count_of_current_device(), 0);
+    h->sms = sm_count_of_current_device();
     if (start == POTTS_START_ORDERED) {
       e = cudaMemsetAsync(h->d_planes, 0, (size_t)(2 * h->plane_bytes),
                           h->stream);
@@ -260,6 +260,7 @@ int potts_sweep(potts_h h, double beta, int64_t nsweeps, uint64_t *out_counts) {
     HT = heat_table(W, m);
   }
   const int64_t rec_len = 1 + q;
+  const TileGeom G = pass_geom(h->L, h->H, q, h->layout, h->update, h->sms);
   PassArgs A[2];
   for (int c = 0; c < 2; ++c) {
     A[c].own = h->d_planes + (c ? h->plane_bytes : 0);
@@ -296,10 +297,10 @@ int potts_sweep(potts_h h, double beta, int64_t nsweeps, uint64_t *out_counts) {
         A[c].t_lo = (uint32_t)t;
         A[c].t_hi = (uint32_t)(t >> 32);
         if (hb)
-          POTTS_CK(launch_pass_hb(A[c], HT, h->geom, h->d_rec + s * rec_len,
+          POTTS_CK(launch_pass_hb(A[c], HT, G, h->d_rec + s * rec_len,
                                   h->stream));
         else
-          POTTS_CK(launch_pass(A[c], T, h->geom, h->d_rec + s * rec_len,
+          POTTS_CK(launch_pass(A[c], T, G, h->d_rec + s * rec_len,
                                h->stream));
       }
     }

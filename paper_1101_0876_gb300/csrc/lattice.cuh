@@ -19,7 +19,7 @@ struct potts_lattice {
   unsigned long long *d_rec = nullptr;  // [rec_cap][1+q]
   uint64_t *h_rec = nullptr;            // pinned copy
   int64_t rec_cap = 0;
-  potts::TileGeom geom{};
+  int32_t sms = 1;          // SMs of the handle's device (launch shapes)
   potts_obs obs{};
   int32_t update = POTTS_UPDATE_METROPOLIS;
   int32_t schedule = POTTS_SCHEDULE_TWO_PASS;

@@ -83,7 +83,8 @@ extern "C" int potts_sweep_planes_noalloc(void *white, void *black, int32_t L,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const AcceptTable T = accept_table(thr);
   const int32_t H = L / 2;
-  const TileGeom G = choose_geom(L, H, q, sm_count_of_current_device(), 0);
+  const TileGeom G = pass_geom(L, H, q, kLayoutU8, POTTS_UPDATE_METROPOLIS,
+                               sm_count_of_current_device());
   PassArgs A[2];
   uint8_t *planes[2] = {static_cast<uint8_t *>(white),
                         static_cast<uint8_t *>(black)};

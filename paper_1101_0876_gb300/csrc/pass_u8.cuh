@@ -268,57 +268,83 @@ struct Lay {
   }
 };
 
+// NW consecutive words (4 NW sites) of one plane row as byte words: U8
+// loads them as 16-byte vectors; U4 (NW = 4 only) loads 8 bytes and unpacks.
+template <int LAY, int NW>
+__device__ __forceinline__ void load_words(const uint8_t *p, bool stream,
+                                           uint32_t w[NW]) {
+  if constexpr (LAY == kLayoutU4) {
+    static_assert(NW == 4, "the unpacking walk takes 16 sites per row");
+    Lay<LAY>::load(p, stream, w);
+  } else {
+#pragma unroll
+    for (int v = 0; v < NW / 4; ++v) Lay<LAY>::load(p + 16 * v, stream, w + 4 * v);
+  }
+}
+template <int LAY, int NW>
+__device__ __forceinline__ void store_words(uint8_t *p, const uint32_t w[NW]) {
+  if constexpr (LAY == kLayoutU4) {
+    Lay<LAY>::store(p, w);
+  } else {
+#pragma unroll
+    for (int v = 0; v < NW / 4; ++v) Lay<LAY>::store(p + 16 * v, w + 4 * v);
+  }
+}
+
 // Per-thread walk state: the three other-plane rows around the current row
 // and the current own row (as byte words), plus pointers to the next rows.
-struct Walk {
-  uint32_t Up[4], Ce[4], S[4];
+template <int NW>
+struct WalkT {
+  uint32_t Up[NW], Ce[NW], S[NW];
   const uint8_t *oth_next;  // other plane, row i+1
   const uint8_t *oth_cur;   // other plane, row i
   uint8_t *own_cur;         // own plane, row i
   int32_t i;                // current row
 };
+using Walk = WalkT<4>;
 
-// One row: update the 16 sites of the own row i against Up (i-1), Ce (i),
+// One row: update the 4 NW sites of the own row i against Up (i-1), Ce (i),
 // the freshly loaded row i+1 and the side byte.  LEFT: the side neighbour
 // is at x-1 (row parity + colour even), else at x+1.  xb: byte offset of
 // the window in a row; xl, xr: byte offsets of the words holding the side
 // sites; RB: bytes per plane row.
-template <int QB, bool LEFT, bool COUNTS, bool PAIRS, bool LT0, int LAY>
+template <int QB, bool LEFT, bool COUNTS, bool PAIRS, bool LT0, int LAY,
+          int NW = 4>
 __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
-                                       const uint8_t *tab, Walk &w,
+                                       const uint8_t *tab, WalkT<NW> &w,
                                        int32_t x0, int32_t xb, int32_t xl,
                                        int32_t xr, int32_t RB, bool more,
                                        uint32_t *lane_hist,
                                        uint32_t &ne_acc) {
   using IO = Lay<LAY>;
   const int32_t L = A.L, H = A.H;
-  uint32_t Dw[4];
-  IO::load(w.oth_next, false, Dw);
+  uint32_t Dw[NW];
+  load_words<LAY, NW>(w.oth_next, false, Dw);
   const uint32_t ew = IO::edge(
       __ldg(reinterpret_cast<const uint32_t *>(w.oth_cur - xb +
                                                (LEFT ? xl : xr))),
       LEFT);
   uint8_t *own_next = (w.i + 1 == L) ? A.own + xb : w.own_cur + RB;
-  uint32_t Sn[4] = {w.S[0], w.S[1], w.S[2], w.S[3]};
-  if (more) IO::load(own_next, true, Sn);
+  uint32_t Sn[NW];
+#pragma unroll
+  for (int k = 0; k < NW; ++k) Sn[k] = w.S[k];
+  if (more) load_words<LAY, NW>(own_next, true, Sn);
 
   const uint32_t *Cw = w.Ce;
-  uint32_t Wd[4];
+  uint32_t Wd[NW];
   if (LEFT) {
     Wd[0] = __funnelshift_l(ew, Cw[0], 8);
-    Wd[1] = __funnelshift_l(Cw[0], Cw[1], 8);
-    Wd[2] = __funnelshift_l(Cw[1], Cw[2], 8);
-    Wd[3] = __funnelshift_l(Cw[2], Cw[3], 8);
+#pragma unroll
+    for (int k = 1; k < NW; ++k) Wd[k] = __funnelshift_l(Cw[k - 1], Cw[k], 8);
   } else {
-    Wd[0] = __funnelshift_r(Cw[0], Cw[1], 8);
-    Wd[1] = __funnelshift_r(Cw[1], Cw[2], 8);
-    Wd[2] = __funnelshift_r(Cw[2], Cw[3], 8);
-    Wd[3] = __funnelshift_r(Cw[3], ew, 8);
+#pragma unroll
+    for (int k = 0; k < NW - 1; ++k) Wd[k] = __funnelshift_r(Cw[k], Cw[k + 1], 8);
+    Wd[NW - 1] = __funnelshift_r(Cw[NW - 1], ew, 8);
   }
   const uint32_t g0 = (uint32_t)(((int64_t)(w.i + A.grow0) * H + x0) >> 2);
-  uint32_t Nw[4];
+  uint32_t Nw[NW];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < NW; ++k) {
     const uint4 u = philox10(g0 + (uint32_t)k, A.t_lo, A.colour, A.t_hi, ks);
     const uint64_t r0 = (uint64_t)u.x * A.q, r1 = (uint64_t)u.y * A.q;
     const uint64_t r2 = (uint64_t)u.z * A.q, r3 = (uint64_t)u.w * A.q;
@@ -340,14 +366,14 @@ __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
       ne_acc += __umulhi(nf16, 1u << 28);  // += nf16 >> 4 (<= 4 per byte)
     }
   }
-  IO::store(w.own_cur, Nw);
+  store_words<LAY, NW>(w.own_cur, Nw);
   if (lane_hist) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) hist_word<PAIRS>(lane_hist, Nw[k]);
+    for (int k = 0; k < NW; ++k) hist_word<PAIRS>(lane_hist, Nw[k]);
   }
   // advance
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < NW; ++k) {
     w.Up[k] = w.Ce[k];
     w.Ce[k] = Dw[k];
     w.S[k] = Sn[k];
@@ -359,12 +385,12 @@ __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
   w.i += 1;
 }
 
-// Walks rows [i0, i0 + rows) of the 16-site column starting at site x0 of
+// Walks rows [i0, i0 + rows) of the 4 NW-site column starting at site x0 of
 // the plane of colour COLOUR.  lane_hist (may be null): per-lane histogram
 // counters of the updated sites.  COUNTS (black pass): *ne_total receives
 // the number of unequal (site, neighbour) pairs after the update.
 template <int QB, int COLOUR, bool COUNTS, bool PAIRS, bool LT0,
-          int LAY = kLayoutU8>
+          int LAY = kLayoutU8, int NW = 4>
 __device__ __forceinline__ void walk_column(const PassArgs &A,
                                             const PhiloxKey &ks,
                                             const uint8_t *tab, int32_t x0,
@@ -376,46 +402,51 @@ __device__ __forceinline__ void walk_column(const PassArgs &A,
   const int32_t RB = IO::row_bytes(H);
   const int32_t xb = LAY == kLayoutU4 ? x0 / 2 : x0;
   const int32_t xl = (x0 == 0) ? RB - 4 : xb - 4;  // word holding site x0-1
-  const int32_t xr = (x0 + 16 == H) ? 0 : xb + IO::kChunkBytes;  // x0+16
-  Walk w;
+  const int32_t xr = (x0 + 4 * NW == H) ? 0
+                                        : xb + IO::kChunkBytes * (NW / 4);
+  WalkT<NW> w;
   const int32_t im = (i0 == 0) ? L - 1 : i0 - 1;
   const int32_t ip = (i0 + 1 == L) ? 0 : i0 + 1;
   w.oth_cur = A.other + (int64_t)i0 * RB + xb;
   w.oth_next = A.other + (int64_t)ip * RB + xb;
   w.own_cur = A.own + (int64_t)i0 * RB + xb;
-  IO::load(A.other + (int64_t)im * RB + xb, false, w.Up);
-  IO::load(w.oth_cur, false, w.Ce);
-  IO::load(w.own_cur, true, w.S);
+  load_words<LAY, NW>(A.other + (int64_t)im * RB + xb, false, w.Up);
+  load_words<LAY, NW>(w.oth_cur, false, w.Ce);
+  load_words<LAY, NW>(w.own_cur, true, w.S);
   w.i = i0;
   uint32_t ne_acc = 0;
   int32_t r = 0;
   // Side neighbour at x-1 when (lattice row + colour) is even.  Walks start
   // on even lattice rows when rows is even, so pairs of rows have a fixed
-  // pattern.
+  // pattern.  The black pass's byte counts (at most 4 per word and byte, so
+  // 4 NW per row) are summed across the four bytes by one multiply, whose
+  // top byte must stay below 256: every pair of rows for NW = 4, every row
+  // for NW = 8.
+  auto fold = [&]() {
+    if (COUNTS) {
+      *ne_total += (ne_acc * 0x01010101u) >> 24;
+      ne_acc = 0;
+    }
+  };
   if (((i0 + A.grow0) & 1) == 0) {
     for (; r + 2 <= rows; r += 2) {
-      do_row<QB, COLOUR == 0, COUNTS, PAIRS, LT0, LAY>(
+      do_row<QB, COLOUR == 0, COUNTS, PAIRS, LT0, LAY, NW>(
           A, ks, tab, w, x0, xb, xl, xr, RB, true, lane_hist, ne_acc);
-      do_row<QB, COLOUR == 1, COUNTS, PAIRS, LT0, LAY>(
+      if (NW > 4) fold();
+      do_row<QB, COLOUR == 1, COUNTS, PAIRS, LT0, LAY, NW>(
           A, ks, tab, w, x0, xb, xl, xr, RB, r + 2 < rows, lane_hist, ne_acc);
-      if (COUNTS) {
-        *ne_total += (ne_acc * 0x01010101u) >> 24;
-        ne_acc = 0;
-      }
+      fold();
     }
   }
   for (; r < rows; ++r) {
     const bool left = ((w.i + A.grow0 + COLOUR) & 1) == 0;
     if (left)
-      do_row<QB, true, COUNTS, PAIRS, LT0, LAY>(
+      do_row<QB, true, COUNTS, PAIRS, LT0, LAY, NW>(
           A, ks, tab, w, x0, xb, xl, xr, RB, r + 1 < rows, lane_hist, ne_acc);
     else
-      do_row<QB, false, COUNTS, PAIRS, LT0, LAY>(
+      do_row<QB, false, COUNTS, PAIRS, LT0, LAY, NW>(
           A, ks, tab, w, x0, xb, xl, xr, RB, r + 1 < rows, lane_hist, ne_acc);
-    if (COUNTS) {
-      *ne_total += (ne_acc * 0x01010101u) >> 24;
-      ne_acc = 0;
-    }
+    fold();
   }
 }
 

@@ -88,7 +88,7 @@ int make_strip(int32_t L, int32_t q, int32_t start, uint64_t seed,
       h->h_rec = nullptr;
       return fail(POTTS_ENOMEM, "cudaMallocHost records");
     }
-    h->geom = choose_geom(nrows, h->H, q, sm_count_of_current_device(), 0);
+    h->sms = sm_count_of_current_device();
     POTTS_CK(cudaMemsetAsync(h->d_planes, 0, (size_t)(2 * h->plane_bytes),
                              h->stream));
     if (start == POTTS_START_RANDOM) {
@@ -156,8 +156,12 @@ cudaError_t strip_pass(potts_h s, const Rule &r, int colour,
   A.grow0 = s->row0 - 1;
   A.row_lo = 1;
   A.row_end = s->nrows + 1;
-  if (r.heatbath) return launch_pass_hb(A, r.HT, s->geom, rec, s->stream);
-  return launch_pass(A, r.T, s->geom, rec, s->stream);
+  const TileGeom G = pass_geom(s->nrows, s->H, s->q, s->layout,
+                               r.heatbath ? POTTS_UPDATE_HEATBATH
+                                          : POTTS_UPDATE_METROPOLIS,
+                               s->sms);
+  if (r.heatbath) return launch_pass_hb(A, r.HT, G, rec, s->stream);
+  return launch_pass(A, r.T, G, rec, s->stream);
 }
 
 cudaError_t copy_row(uint8_t *dst, int dst_dev, const uint8_t *src,
