@@ -23,14 +23,33 @@ Metric: ns per spin update (time / (N * sweeps)), whole job, lower is better.
   roofline  the colour-pass kernel against measured HBM bandwidth, 1.5 bytes
             per spin per pass (read own plane, write own plane, read other
             plane once) = 3 bytes per spin per sweep.
-  cpu_baseline  the serial CPU oracle on a bounded sample (one core), plus
-                one oracle instance per host core (aggregate).
+  cpu_baseline  the serial CPU oracle (one core) on one sweep of an
+                L = 16384 lattice (256 MiB, streamed from host DRAM), plus
+                a cache-resident L = 2048 sample and one oracle instance
+                per host core (aggregate).
+  u4            the same workload in the packed 4-bit layout.
+  q15_u8, q15_u4, q96_u8
+                the other paper-scale configurations: q = 15 at L = 32768
+                (both layouts) and q = 96 at L = 16384, at the same three
+                temperatures, device-timed.
+  mid           the L = 4096 heating and cooling ladders (41 temperatures,
+                2000 sweeps each), updates/s.
   heatbath      the same workload with the heat-bath update rule.
   fused         the same workload under the fused sweep schedule (both
                 colour passes in one kernel, 2 bytes per spin per sweep).
+  batched       the 256-lattice batched configuration.
+  served        the first 200 requests of the served stream at 200 req/s
+                (offered load above capacity: latency measures the backlog);
+  served_subcap the same requests arriving at the rate that offers about
+                0.8 of the measured served throughput (latency measures
+                service);
+  served_full   the whole 10000-request stream at 200 req/s.
 
-With torchrun (N > 1) each rank sweeps its own replica (weak scaling, no
-data-path collective); the time is the max over ranks.
+With --gpus N > 1 under torchrun (one rank per GPU) the paper-scale lattice
+is split into N row strips, one per rank, with the halo rows exchanged by
+NCCL before every colour pass and the counts all-reduced after every sweep
+(strong scaling); the time is the max over ranks.  --gpus N without torchrun
+splits it over N devices of this process.
 """
 from __future__ import annotations
 
@@ -53,7 +72,7 @@ METRIC = "ns/spin-update @L=32768 q=9 (frac HBM peak)"
 UNIT = "ns/update"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "colour_pass_L32768_q9_traffic.md")
-KERNEL_SOURCES = ["pass_u8.cuh", "philox.cuh", "kernels.cu"]
+KERNEL_SOURCES = ["pass_u8.cuh", "pass_u4.cuh", "philox.cuh", "kernels.cu"]
 
 
 def kernel_hash() -> str:
@@ -92,14 +111,16 @@ def traffic_per_launch(L: int):
 
 
 FULLSET_FILE = os.path.join(ROOT, "profiles", "colour_pass_L16384_q9.md")
+U4_FULLSET_FILE = os.path.join(ROOT, "profiles",
+                               "colour_pass_u4_L16384_q9.md")
 
 
-def instructions_per_site():
+def instructions_per_site(path=FULLSET_FILE):
     """Thread instructions per updated site of the white and black passes
-    from the committed full-set ncu summary (the ALU check beside the HBM
+    from a committed full-set ncu summary (the ALU check beside the HBM
     roofline); None when the kernel sources changed since the capture."""
     try:
-        text = open(FULLSET_FILE).read()
+        text = open(path).read()
     except OSError:
         return None
     mh = re.search(r"Kernel sources hash:\s*([0-9a-f]+)", text)
@@ -108,7 +129,7 @@ def instructions_per_site():
     if not (mh and mi) or mh.group(1) != kernel_hash():
         return None
     return {"white": float(mi.group(1)), "black": float(mi.group(2)),
-            "source": "profiles/colour_pass_L16384_q9.md (ncu, L = 16384)"}
+            "source": f"profiles/{os.path.basename(path)} (ncu, L = 16384)"}
 
 
 # GB300 instruction issue: one warp instruction per clock on each of the
@@ -275,6 +296,152 @@ def cpu_oracle_all_cores(L: int, q: int, beta: float, sweeps: int,
     return upd / wall, n, wall
 
 
+# ------------------------------------------------------- row strips
+def run_strips_ranks(args):
+    """N > 1 under torchrun, one rank per GPU: the paper-scale lattice
+    (L = 32768, q = 9, seed 11) split into N row strips, strip r on rank r;
+    before each colour pass neighbouring ranks exchange one halo row (NCCL
+    send/receive), after each sweep the (1 + q) counts are summed
+    (all-reduce).  Strong scaling: the whole job is one lattice; value =
+    time per spin update of the whole lattice, max over ranks."""
+    import numpy as np
+    import torch
+
+    from paper_1101_0876_gb300 import potts, strips, workloads
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    init_dist(ws, "nccl")
+    cfg = workloads.PAPER_Q9
+    L, q = args.L or cfg.L, cfg.q
+    N = L * L
+    row0, nrows = strips.partition(L, ws)[rank]
+    band = strips.StripBand(L, q, potts.START_RANDOM, cfg.seed, row0, nrows,
+                            device=local)
+    sw = strips.StripSweeper(band, rank, ws)
+    betas = [workloads.beta_at(q, t) for t in cfg.t_over_tc]
+    K, W = args.steps, args.warmup
+    seg = [K // 3 + (1 if k < K % 3 else 0) for k in range(3)]
+    recs = torch.zeros((max(K, 1), 1 + q), dtype=torch.int64, device=dev)
+    for _ in range(W):
+        sw.sweep(betas[0])
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    st = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    k = 0
+    for b, n in zip(betas, seg):
+        for _ in range(n):
+            sw.sweep(b, record=recs[k])
+            k += 1
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    dev_ms = e0.elapsed_time(e1)
+    barrier(ws)
+    dev_ms_max = reduce_max(dev_ms, ws, dev)
+    # end to end: one sweep per step, its record read back to the host
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for b, n in zip(betas, seg):
+        for _ in range(n):
+            sw.sweep(b).cpu()
+    e2e_s = time.perf_counter() - t0
+    barrier(ws)
+    e2e_max = reduce_max(e2e_s, ws, dev)
+    clocks.stop()
+    B_last = int(recs[K - 1, 0].item())
+    band.close()
+    if rank != 0:
+        return None
+    hbm, kind = measured_peaks()
+    pass_ms = dev_ms_max / (2 * K)
+    bytes_per_launch = 1.5 * nrows * L
+    achieved = bytes_per_launch / (pass_ms * 1e-3) / 1e9
+    return {
+        "metric": METRIC, "value": dev_ms_max * 1e6 / (N * K), "unit": UNIT,
+        "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": dev_ms_max / K, "higher_is_better": False,
+        "scaling": "strong", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (random start from Philox, seed 11)",
+        "config": {"workload": f"paper_scale_L{L}_q{q}_u8", "L": L, "q": q,
+                   "start": "random", "seed": cfg.seed,
+                   "t_over_tc": list(cfg.t_over_tc),
+                   "parallelism": f"row_strips{ws}",
+                   "strip_rows": nrows,
+                   "exchange": "one halo row per neighbour and colour pass "
+                               "(NCCL send/recv), (1+q) counts all-reduced "
+                               "per sweep",
+                   "l2": "no flush: each strip's planes exceed L2 at N <= 8"},
+        "updates_per_s": N * K / (dev_ms_max * 1e-3),
+        "e2e": {"value": e2e_max * 1e9 / (N * K), "unit": UNIT,
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": (1 + q) * 8},
+        "gpu_launches": 2 * K,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "peak_source": f"{kind} hbm_gbs",
+                     "kernel": "colour pass of one strip (per GPU), halo "
+                               "exchange and all-reduce included in the "
+                               "time", "bytes_per_launch": bytes_per_launch},
+        "last_bonds": B_last,
+        "clocks": clocks.summary(),
+    }
+
+
+def run_strips_local(args):
+    """--gpus N without torchrun: the paper-scale lattice split into N row
+    strips on devices 0..N-1 of this one process (potts_create_sharded; halo
+    rows by device-to-device copies).  Needs N visible devices."""
+    import torch
+
+    from paper_1101_0876_gb300 import potts, workloads
+    n = int(args.gpus)
+    have = torch.cuda.device_count()
+    if have < n:
+        raise SystemExit(f"--gpus {n} without torchrun needs {n} visible "
+                         f"devices, found {have}")
+    cfg = workloads.PAPER_Q9
+    L, q = args.L or cfg.L, cfg.q
+    N = L * L
+    lat = potts.Lattice(L, q, potts.START_RANDOM, cfg.seed, nstrips=n,
+                        devices=list(range(n)))
+    betas = [workloads.beta_at(q, t) for t in cfg.t_over_tc]
+    K, W = args.steps, args.warmup
+    seg = [K // 3 + (1 if k < K % 3 else 0) for k in range(3)]
+    lat.sweep(betas[0], W, records=False)
+    for d in range(n):
+        torch.cuda.synchronize(d)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    for b, k in zip(betas, seg):
+        lat.sweep(b, k)
+    secs = time.perf_counter() - t0
+    clocks.stop()
+    lat.close()
+    return {
+        "metric": METRIC, "value": secs * 1e9 / (N * K), "unit": UNIT,
+        "n_gpus": n, "steps": K, "warmup": W, "ms_per_step": secs * 1e3 / K,
+        "higher_is_better": False, "scaling": "strong", "vs_baseline": None,
+        "dtype": "u8", "data": "synthetic (random start from Philox, seed 11)",
+        "config": {"workload": f"paper_scale_L{L}_q{q}_u8", "L": L, "q": q,
+                   "parallelism": f"row_strips{n} (one process)"},
+        "updates_per_s": N * K / secs,
+        "e2e": {"value": secs * 1e9 / (N * K), "unit": UNIT,
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": (1 + q) * 8},
+        "gpu_launches": 2 * n * K,
+        "timing": "wall clock around potts_sweep (records to host)",
+        "clocks": clocks.summary(),
+    }
+
+
 # --------------------------------------------------------- our arm
 def run_ours(args):
     import numpy as np
@@ -283,6 +450,10 @@ def run_ours(args):
     from paper_1101_0876_gb300 import potts, workloads
 
     ws, rank, local = dist_env()
+    if ws > 1:
+        return run_strips_ranks(args)
+    if args.gpus > 1:
+        return run_strips_local(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     init_dist(ws, "nccl")
@@ -313,10 +484,10 @@ def run_ours(args):
     # ---- device-timed region
     barrier(ws)
     torch.cuda.synchronize(dev)
-    # each temperature's steps in two halves, an event at every boundary:
-    # the per-part times give a median over six repetitions beside the total
-    parts = [(b, h) for b, n in zip(betas, seg) for h in (n // 2, n - n // 2)
-             if h > 0]
+    # one call per temperature (the records of its sweeps come back to the
+    # host at the end of the call), an event at every boundary: the
+    # per-temperature times are reported beside the total
+    parts = [(b, n) for b, n in zip(betas, seg) if n > 0]
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)]
     evs[0].record(stream)
     off = 0
@@ -364,7 +535,9 @@ def run_ours(args):
         job = {"value": job_s * 1e9 / (ws * N * K), "unit": UNIT,
                "h2d_bytes_per_step": N / K, "d2h_bytes_per_step":
                N / K + (1 + q) * 8, "note": "set_state upload + K sweeps + "
-               "get_spins download, amortised per step"}
+               "get_spins download, amortised per step: the 1 GiB upload and "
+               "download are a fixed cost, so this figure depends on K (it "
+               "approaches e2e as K grows)"}
 
     if rank != 0:
         return None
@@ -386,8 +559,10 @@ def run_ours(args):
         "repeats": {"n": len(part_ms),
                     "ms_per_step": [round(x, 5) for x in part_ms],
                     "median_ms_per_step": float(np.median(part_ms)),
-                    "note": "the timed steps in six consecutive parts (two "
-                            "per temperature), CUDA events between parts"},
+                    "note": "the timed steps in three consecutive parts "
+                            "(one potts_sweep call per temperature, records "
+                            "to host at the end of each), CUDA events "
+                            "between parts"},
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
@@ -397,7 +572,7 @@ def run_ours(args):
                    "L": L, "q": q, "start": "random", "seed": cfg.seed,
                    "t_over_tc": list(temps), "sweeps_per_step": 1,
                    "l2": "no flush: 2 GiB of planes per sweep > 126 MB L2",
-                   "parallelism": f"replicas{ws}"},
+                   "parallelism": "single GPU"},
         "updates_per_s": ws * N * K / (dev_ms_max * 1e-3),
         "e2e": {"value": e2e_s_max * 1e9 / (ws * N * K), "unit": UNIT,
                 "h2d_bytes_per_step": 0,
@@ -416,29 +591,60 @@ def run_ours(args):
         "roofline_alu": alu_roofline(N * K / (dev_ms * 1e-3)),
         "clocks": clocks.summary(),
     }
-    if ws == 1 and not args.no_u4:
+    if not args.no_u4:
         lat.close()
-        line["u4"] = measure_u4(args, L, q, betas)
-    if ws == 1 and not args.no_heatbath:
+        line["u4"] = measure_config(args, L, q, potts.LAYOUT_U4, temps,
+                                    max(10, args.steps))
+        line["u4"]["inst_per_site"] = instructions_per_site(U4_FULLSET_FILE)
+    if not args.no_configs:
+        lat.close()
+        c15, c96 = workloads.PAPER_Q15, workloads.PAPER_Q96
+        n_t = max(10, args.steps)   # sweeps per temperature and call
+        line["q15_u8"] = measure_config(args, c15.L, c15.q, potts.LAYOUT_U8,
+                                        c15.t_over_tc, n_t)
+        line["q15_u4"] = measure_config(args, c15.L, c15.q, potts.LAYOUT_U4,
+                                        c15.t_over_tc, n_t)
+        line["q96_u8"] = measure_config(args, c96.L, c96.q, potts.LAYOUT_U8,
+                                        c96.t_over_tc, n_t)
+        line["mid"] = measure_mid(args)
+    if not args.no_heatbath:
         lat.close()
         line["heatbath"] = measure_heatbath(args, L, q, betas)
-    if ws == 1 and not args.no_fused:
+    if not args.no_fused:
         lat.close()
         line["fused"] = measure_fused(args, L, q, betas, ns)
-    if ws == 1 and not args.no_batched:
+    if not args.no_batched:
         lat.close()
         line["batched"] = measure_batched(args, line["updates_per_s"])
-    if ws == 1 and not args.no_served:
+    if not args.no_served:
         lat.close()
         line["served"] = measure_served(args, line["updates_per_s"])
-    if not args.no_cpu_baseline and ws == 1:
-        Lc, sweeps = args.cpu_L, args.cpu_sweeps
-        nsu, dt = cpu_oracle_ns_per_update(Lc, q, betas[1], sweeps, cfg.seed)
+        # below capacity: arrivals at the rate that offers ~0.8 of the
+        # throughput the saturated server just delivered
+        cap = line["served"]["updates_per_s"]
+        per_req = (line["served"]["offered_updates_per_s"]
+                   / args.served_rate)
+        rate = 0.8 * cap / per_req
+        line["served_subcap"] = measure_served(
+            args, line["updates_per_s"], rate=rate)
+        if not args.no_served_full:
+            line["served_full"] = measure_served(
+                args, line["updates_per_s"], n=10000, rate=args.served_rate)
+    if not args.no_cpu_baseline:
+        Lc = args.cpu_L_dram
+        nsu, dt = cpu_oracle_ns_per_update(Lc, q, betas[1], 1, cfg.seed)
         line["cpu_baseline"] = {
             "value": nsu, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"serial oracle, L={Lc} q={q} random start at T_c, "
-                      f"{sweeps} sweeps ({dt:.1f} s); per-update cost of the "
-                      f"serial raster loop does not depend on L"}
+            "sample": f"serial oracle, one sweep of an L={Lc} q={q} lattice "
+                      f"(random start, T_c; {Lc * Lc // 2**20} MiB, larger "
+                      f"than the host's caches; {dt:.1f} s)"}
+        Lc, sweeps = args.cpu_L, args.cpu_sweeps
+        nsu, dt = cpu_oracle_ns_per_update(Lc, q, betas[1], sweeps, cfg.seed)
+        line["cpu_baseline"]["cache_resident"] = {
+            "value": nsu, "unit": UNIT, "cores": 1,
+            "sample": f"serial oracle, L={Lc} q={q} ({Lc * Lc // 2**20} "
+                      f"MiB) random start at T_c, {sweeps} sweeps "
+                      f"({dt:.1f} s)"}
         ups, ncores, wall = cpu_oracle_all_cores(512, q, betas[1],
                                                  args.cpu_sweeps_all, cfg.seed)
         line["cpu_baseline"]["all_cores"] = {
@@ -450,33 +656,66 @@ def run_ours(args):
     return line
 
 
-# ------------------------------------------------- packed 4-bit layout
-def measure_u4(args, L, q, betas):
-    """The same workload in the packed 4-bit layout (q <= 16): 1.5 bytes
-    per site per sweep, device-timed like `value`."""
+# -------------------------------------------- single-lattice configurations
+def measure_config(args, L, q, layout, t_over_tc, sweeps_per_t, seed=11):
+    """One paper-scale configuration (random start, seed 11): sweeps_per_t
+    sweeps at each temperature in turn, device-timed with CUDA events per
+    temperature; the lattice exceeds L2, so no flush is needed."""
     import torch
-    from paper_1101_0876_gb300 import potts
+    from paper_1101_0876_gb300 import potts, workloads
     stream = torch.cuda.Stream()
-    lat = potts.Lattice(L, q, potts.START_RANDOM, 11, layout=potts.LAYOUT_U4)
+    lat = potts.Lattice(L, q, potts.START_RANDOM, seed, layout=layout)
     lat.set_stream(stream.cuda_stream)
+    betas = [workloads.beta_at(q, t) for t in t_over_tc]
     lat.sweep(betas[0], 3, records=False)
-    n = max(3, args.steps // 2)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(betas) + 1)]
     torch.cuda.synchronize()
-    e0.record(stream)
-    lat.sweep(betas[1], n)
-    e1.record(stream)
+    evs[0].record(stream)
+    for b, ev in zip(betas, evs[1:]):
+        lat.sweep(b, sweeps_per_t)
+        ev.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(len(betas))]
     lat.close()
     N = L * L
-    hbm, _ = measured_peaks()
-    gbs = 1.5 * N * n / (ms * 1e-3) / 1e9
-    return {"value": ms * 1e6 / (N * n), "unit": UNIT, "sweeps": n,
-            "updates_per_s": N * n / (ms * 1e-3),
-            "bytes_per_update": 1.5, "achieved_gbs": gbs,
-            "frac_hbm": gbs / hbm}
+    bpu = 1.5 if layout == potts.LAYOUT_U4 else 3.0
+    tot = sum(ms)
+    n = sweeps_per_t * len(betas)
+    hbm, kind = measured_peaks()
+    gbs = bpu * N * n / (tot * 1e-3) / 1e9
+    return {"value": tot * 1e6 / (N * n), "unit": UNIT, "L": L, "q": q,
+            "layout": "u4" if layout == potts.LAYOUT_U4 else "u8",
+            "t_over_tc": list(t_over_tc), "sweeps_per_t": sweeps_per_t,
+            "ns_per_update_per_t": [x * 1e6 / (N * sweeps_per_t) for x in ms],
+            "updates_per_s": N * n / (tot * 1e-3),
+            "bytes_per_update": bpu, "achieved_gbs": gbs,
+            "frac_hbm": gbs / hbm, "peak_source": f"{kind} hbm_gbs"}
+
+
+def measure_mid(args):
+    """The mid configuration (L = 4096, q = 9): heating from the ordered
+    start and cooling from the random start over 41 temperatures in
+    [0.97, 1.03] T_c, 2000 sweeps each, seed 7, records formed every sweep
+    (FP64 e and m on the host).  The 16 MiB lattice stays in L2, so the
+    figure is updates/s, not an HBM fraction."""
+    from paper_1101_0876_gb300 import protocol, workloads
+    cfg = workloads.MID
+    L, q = cfg["L"], cfg["q"]
+    temps = [workloads.tc(q) * t for t in cfg["ladder"]]
+    n = args.mid_sweeps
+    heat = protocol.ladder(L, q, temps, 0, n, 1, protocol.START_ORDERED,
+                           cfg["seed"])
+    cool = protocol.ladder(L, q, temps[::-1], 0, n, 1, protocol.START_RANDOM,
+                           cfg["seed"])
+    secs = heat[1] + cool[1]
+    upd = heat[2] + cool[2]
+    return {"value": secs * 1e9 / upd, "unit": UNIT,
+            "updates_per_s": upd / secs, "seconds": secs, "L": L, "q": q,
+            "temperatures": len(temps), "sweeps_per_t": n,
+            "timing": "wall clock around the heating and cooling runs "
+                      "(potts_sweep per temperature, records to host)",
+            "heating_e_at_tc": heat[0][len(temps) // 2]["e"],
+            "cooling_e_at_tc": cool[0][len(temps) // 2]["e"]}
 
 
 # ------------------------------------------------------ heat-bath rule
@@ -562,15 +801,17 @@ def measure_batched(args, single_updates_per_s):
             "timing": "wall clock around potts_batch_sweep, records to host"}
 
 
-def measure_served(args, single_updates_per_s):
-    """The served configuration, bounded: the first `served_requests`
-    requests of the Poisson stream (200 req/s; L log-uniform in
-    [128, 8192]; q in {6, 9, 15, 24, 96}; T in [0.97, 1.03] T_c; nsweeps in
-    [100, 5000]; seed = request id), submitted at their arrival times to a
-    continuous-batching server with a 120 GB budget; latency = time the
-    last record was polled - arrival time."""
+def measure_served(args, single_updates_per_s, n=None, rate=None):
+    """The served configuration: the first n (default `served_requests`)
+    requests of the Poisson stream (`rate` req/s, default 200; L
+    log-uniform in [128, 8192]; q in {6, 9, 15, 24, 96}; T in [0.97, 1.03]
+    T_c; nsweeps in [100, 5000]; seed = request id), submitted at their
+    arrival times to a continuous-batching server with a 120 GB budget;
+    latency = time the last record was polled - arrival time."""
     from paper_1101_0876_gb300 import potts, workloads
-    reqs = workloads.served(n=args.served_requests, rate_hz=args.served_rate)
+    n = args.served_requests if n is None else int(n)
+    rate = args.served_rate if rate is None else float(rate)
+    reqs = workloads.served(n=n, rate_hz=rate)
     srv = potts.Server(hbm_budget_bytes=120 * 10**9,
                        max_slots=args.served_slots,
                        sweeps_per_step=args.served_k,
@@ -611,7 +852,7 @@ def measure_served(args, single_updates_per_s):
             "p50_ms": pct(50), "p99_ms": pct(99), "max_ms": lat_ms[-1],
             "offered_updates_per_s": offered,
             "slots": args.served_slots, "sweeps_per_step": args.served_k,
-            "rate_hz": args.served_rate, "policy": args.served_policy,
+            "rate_hz": rate, "policy": args.served_policy,
             "steps": st["steps"],
             "note": ("offered load exceeds capacity: latency grows with the "
                      "backlog (saturated server)")
@@ -667,6 +908,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-job", action="store_true")
     ap.add_argument("--cpu-L", type=int, default=2048)
+    ap.add_argument("--cpu-L-dram", type=int, default=16384,
+                    help="lattice of the one-sweep CPU oracle sample that "
+                         "streams from host DRAM")
     ap.add_argument("--cpu-sweeps", type=int, default=40)
     ap.add_argument("--cpu-sweeps-all", type=int, default=300,
                     help="sweeps per core of the all-cores oracle baseline")
@@ -676,6 +920,11 @@ def main():
     ap.add_argument("--no-fused", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-served-full", action="store_true",
+                    help="skip the full 10000-request served stream")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the q=15, q=96 and mid configurations")
+    ap.add_argument("--mid-sweeps", type=int, default=2000)
     ap.add_argument("--batch-sweeps", type=int, default=500)
     ap.add_argument("--served-requests", type=int, default=200)
     ap.add_argument("--served-slots", type=int, default=64)

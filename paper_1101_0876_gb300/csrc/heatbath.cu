@@ -32,12 +32,9 @@ __global__ void __launch_bounds__(kPassThreads, QB <= 6 ? 4 : POTTS_HB_MINB)
   __shared__ uint32_t s_fold[16];
   const uint32_t tid = threadIdx.x;
   const uint32_t bins = PAIRS ? (uint32_t)kHbPairBins : A.hist_bins;
-  const bool hist = rec != nullptr;
-  if (hist) {
-    for (uint32_t v = tid; v < bins * 32u; v += kPassThreads) s_hist[v] = 0;
-    if (tid < 16) s_fold[tid] = 0;
-    if (tid == 0) s_sat = 0;
-  }
+  for (uint32_t v = tid; v < bins * 32u; v += kPassThreads) s_hist[v] = 0;
+  if (tid < 16) s_fold[tid] = 0;
+  if (tid == 0) s_sat = 0;
   hb_build_table(s_W, T.W, A.q, T.m, tid);  // ends with a barrier
   pdl_wait_previous();
 
@@ -51,13 +48,11 @@ __global__ void __launch_bounds__(kPassThreads, QB <= 6 ? 4 : POTTS_HB_MINB)
       if (i0 >= A.row_end) continue;
       const int32_t rows = min(G.TR, A.row_end - i0);
       hb_walk_column<QB, COLOUR, COUNTS, PAIRS, LAY>(
-          A, ks, s_W, T.m, chunk * 16, i0, rows,
-          hist ? s_hist + (tid & 31u) : nullptr, &ne);
+          A, ks, s_W, T.m, chunk * 16, i0, rows, s_hist + (tid & 31u), &ne);
       rows_done += (uint32_t)rows;
     }
   }
   pdl_release_next();
-  if (!hist) return;
   if (COUNTS) {
     uint32_t sat = 64u * rows_done - ne;
 #pragma unroll
@@ -95,8 +90,7 @@ cudaError_t launch_hb_c(const PassArgs &A, const HeatTable &T,
                         cudaStream_t st) {
   dim3 grid(G.gx, G.gy), block(kPassThreads);
   const size_t smem =
-      rec ? (size_t)(PAIRS ? kHbPairBins : A.hist_bins) * 32u * sizeof(uint32_t)
-          : 0;
+      (size_t)(PAIRS ? kHbPairBins : A.hist_bins) * 32u * sizeof(uint32_t);
   return launch_pdl(hb_pass_kernel<QB, COLOUR, PAIRS, LAY>, grid, block,
                     smem, st, A, T, G, rec);
 }
@@ -167,6 +161,7 @@ HeatTable heat_table(const uint64_t W[5], int32_t m) {
 cudaError_t launch_pass_hb(const PassArgs &A, const HeatTable &T,
                            const TileGeom &G, unsigned long long *rec,
                            cudaStream_t st) {
+  if (!rec) return cudaErrorInvalidValue;
   if (A.layout == kLayoutU4) {
     if (A.q > 16) return cudaErrorInvalidValue;
     return launch_hb_lay<4, kLayoutU4>(A, T, G, rec, st);

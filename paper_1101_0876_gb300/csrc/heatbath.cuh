@@ -229,9 +229,9 @@ __device__ __forceinline__ void hb_row(const PassArgs &A, const PhiloxKey &ks,
       __ldg(reinterpret_cast<const uint32_t *>(w.oth_cur - xb +
                                                (LEFT ? xl : xr))),
       LEFT);
+  // the rule never reads the site's own spin, so the own plane is only
+  // written (1 byte per site per pass instead of 1.5)
   uint8_t *own_next = (w.i + 1 == L) ? A.own + xb : w.own_cur + RB;
-  uint32_t Sn[4] = {w.S[0], w.S[1], w.S[2], w.S[3]};
-  if (more) IO::load(own_next, true, Sn);
   const uint32_t *Cw = w.Ce;
   uint32_t Wd[4];
   if (LEFT) {
@@ -273,15 +273,12 @@ __device__ __forceinline__ void hb_row(const PassArgs &A, const PhiloxKey &ks,
     }
   }
   IO::store(w.own_cur, Nw);
-  if (lane_hist) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) hist_word<PAIRS>(lane_hist, Nw[k]);
-  }
+  for (int k = 0; k < 4; ++k) hist_word<PAIRS>(lane_hist, Nw[k]);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     w.Up[k] = w.Ce[k];
     w.Ce[k] = Dw[k];
-    w.S[k] = Sn[k];
   }
   w.oth_cur = w.oth_next;
   w.oth_next = (w.i + 2 >= L) ? A.other + xb + (int64_t)(w.i + 2 - L) * RB
@@ -310,7 +307,6 @@ __device__ __forceinline__ void hb_walk_column(
   w.own_cur = A.own + (int64_t)i0 * RB + xb;
   IO::load(A.other + (int64_t)im * RB + xb, false, w.Up);
   IO::load(w.oth_cur, false, w.Ce);
-  IO::load(w.own_cur, true, w.S);
   w.i = i0;
   uint32_t ne_acc = 0;
   int32_t r = 0;

@@ -124,7 +124,7 @@ bool heatbath_table(double beta, int32_t q, uint64_t W[5], int32_t *m);
 HeatTable heat_table(const uint64_t W[5], int32_t m);
 
 // ----------------------------------------------------------- launches
-// One colour pass of one lattice.  rec (may be null) receives, added
+// One colour pass of one lattice.  rec (not null) receives, added
 // atomically, the histogram of the updated sites and, on the black pass, B;
 // the record {B, hist[q]} of a sweep must start at zero.
 cudaError_t launch_pass(const PassArgs &A, const AcceptTable &T,

@@ -21,9 +21,8 @@ namespace potts {
 constexpr int kPairBins = 256;
 
 // Resident CTAs per SM the pass kernels are compiled for: 128 threads x
-// 80 registers for 16 sites per thread, 168 for 32 (where the longer rows
-// save per-row work: 1.208 against 1.241 ps per update at L = 32768), and
-// 128 for the nibble pass.
+// 80 registers for 16 sites per thread, 168 for 32 (the longer rows save
+// per-row work), and 128 for the nibble pass.
 constexpr int kMinb32 = 3, kMinbNib = 4;
 
 template <int QB, int COLOUR, bool PAIRS, bool LT0, int LAY, int NW>
@@ -38,14 +37,11 @@ __global__ void __launch_bounds__(kPassThreads,
   __shared__ uint32_t s_fold[16];
   const uint32_t tid = threadIdx.x;
   const uint32_t bins = PAIRS ? (uint32_t)kPairBins : A.hist_bins;
-  const bool hist = rec != nullptr;
   for (uint32_t i = tid; i < (uint32_t)kTabWords; i += kPassThreads)
     s_tab[i] = (i % 4u == 0 && i / 4u < 9u) ? Tin.tab[i / 4u] : 0u;
-  if (hist) {
-    for (uint32_t v = tid; v < bins * 32u; v += kPassThreads) s_hist[v] = 0;
-    if (tid < 16) s_fold[tid] = 0;
-    if (tid == 0) s_sat = 0;
-  }
+  for (uint32_t v = tid; v < bins * 32u; v += kPassThreads) s_hist[v] = 0;
+  if (tid < 16) s_fold[tid] = 0;
+  if (tid == 0) s_sat = 0;
   __syncthreads();
   pdl_wait_previous();  // the other plane is the previous pass's output
 
@@ -60,12 +56,11 @@ __global__ void __launch_bounds__(kPassThreads,
       const int32_t rows = min(G.TR, A.row_end - i0);
       walk_column<QB, COLOUR, COUNTS, PAIRS, LT0, LAY, NW>(
           A, ks, reinterpret_cast<const uint8_t *>(s_tab), chunk * 4 * NW, i0,
-          rows, hist ? s_hist + (tid & 31u) : nullptr, &ne);
+          rows, s_hist + (tid & 31u), &ne);
       rows_done += (uint32_t)rows;
     }
   }
   pdl_release_next();
-  if (!hist) return;
   if (COUNTS) {
     uint32_t sat = 16u * NW * rows_done - ne;
 #pragma unroll
@@ -163,8 +158,7 @@ static cudaError_t launch_c(const PassArgs &A, const AcceptTable &T,
                             cudaStream_t st) {
   dim3 grid(G.gx, G.gy), block(kPassThreads);
   const size_t smem =
-      rec ? (size_t)(PAIRS ? kPairBins : A.hist_bins) * 32u * sizeof(uint32_t)
-          : 0;
+      (size_t)(PAIRS ? kPairBins : A.hist_bins) * 32u * sizeof(uint32_t);
   if (T.rule_lt0)
     return launch_pdl(pass_kernel<QB, COLOUR, PAIRS, true, LAY, NW>, grid,
                       block, smem, st, A, T, G, rec);
@@ -207,9 +201,9 @@ static cudaError_t launch_u4(const PassArgs &A, const AcceptTable &T,
 cudaError_t launch_pass(const PassArgs &A, const AcceptTable &T,
                         const TileGeom &G, unsigned long long *rec,
                         cudaStream_t st) {
+  if (!rec) return cudaErrorInvalidValue;
   if (A.layout == kLayoutU4) {
-    // the nibble pass always histograms into its pair bins
-    if (A.q > 16 || !G.nibble || !rec) return cudaErrorInvalidValue;
+    if (A.q > 16 || !G.nibble) return cudaErrorInvalidValue;
     return launch_u4(A, T, G, rec, st);
   }
   if (G.nibble || (G.sites == 32 && A.H % 32)) return cudaErrorInvalidValue;
@@ -292,9 +286,11 @@ TileGeom pass_geom(int32_t nrows, int32_t H, int32_t q, int32_t layout,
     g.nibble = 1;
     return g;
   }
-  if (H % 32 == 0) {
-    // one state per bin: with 32 sites per thread the pair bins' 32 KB of
-    // shared memory per CTA buy nothing (1.2102 against 1.2076 ps)
+  if (H % 32 == 0 && q <= 16) {
+    // 32 sites per thread for the cheap q <= 16 rule (1.205 against 1.232
+    // ps per update at L = 32768, q = 9; at q = 96 the longer rows are 0.7 %
+    // slower), one state per bin: there the pair bins' 32 KB of shared
+    // memory per CTA buy nothing (1.2102 against 1.2076 ps)
     TileGeom g = choose_geom(nrows, H, q, sm_count, 0, 32, kMinb32);
     g.pairs = 0;
     return g;

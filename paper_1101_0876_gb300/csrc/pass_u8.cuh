@@ -300,6 +300,7 @@ struct WalkT {
   const uint8_t *oth_cur;   // other plane, row i
   uint8_t *own_cur;         // own plane, row i
   int32_t i;                // current row
+  uint32_t g0;              // Philox counter word 0 of the window's first site
 };
 using Walk = WalkT<4>;
 
@@ -307,7 +308,8 @@ using Walk = WalkT<4>;
 // the freshly loaded row i+1 and the side byte.  LEFT: the side neighbour
 // is at x-1 (row parity + colour even), else at x+1.  xb: byte offset of
 // the window in a row; xl, xr: byte offsets of the words holding the side
-// sites; RB: bytes per plane row.
+// sites; RB: bytes per plane row; lane_hist: the lane's histogram counters
+// (not null).
 template <int QB, bool LEFT, bool COUNTS, bool PAIRS, bool LT0, int LAY,
           int NW = 4>
 __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
@@ -341,11 +343,10 @@ __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
     for (int k = 0; k < NW - 1; ++k) Wd[k] = __funnelshift_r(Cw[k], Cw[k + 1], 8);
     Wd[NW - 1] = __funnelshift_r(Cw[NW - 1], ew, 8);
   }
-  const uint32_t g0 = (uint32_t)(((int64_t)(w.i + A.grow0) * H + x0) >> 2);
   uint32_t Nw[NW];
 #pragma unroll
   for (int k = 0; k < NW; ++k) {
-    const uint4 u = philox10(g0 + (uint32_t)k, A.t_lo, A.colour, A.t_hi, ks);
+    const uint4 u = philox10(w.g0 + (uint32_t)k, A.t_lo, A.colour, A.t_hi, ks);
     const uint64_t r0 = (uint64_t)u.x * A.q, r1 = (uint64_t)u.y * A.q;
     const uint64_t r2 = (uint64_t)u.z * A.q, r3 = (uint64_t)u.w * A.q;
     const uint32_t P = pack4((uint32_t)(r0 >> 32), (uint32_t)(r1 >> 32),
@@ -367,10 +368,8 @@ __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
     }
   }
   store_words<LAY, NW>(w.own_cur, Nw);
-  if (lane_hist) {
 #pragma unroll
-    for (int k = 0; k < NW; ++k) hist_word<PAIRS>(lane_hist, Nw[k]);
-  }
+  for (int k = 0; k < NW; ++k) hist_word<PAIRS>(lane_hist, Nw[k]);
   // advance
 #pragma unroll
   for (int k = 0; k < NW; ++k) {
@@ -383,11 +382,12 @@ __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
                               : w.oth_next + RB;
   w.own_cur = own_next;
   w.i += 1;
+  w.g0 += (uint32_t)(H >> 2);  // walks never wrap past the last row
 }
 
 // Walks rows [i0, i0 + rows) of the 4 NW-site column starting at site x0 of
-// the plane of colour COLOUR.  lane_hist (may be null): per-lane histogram
-// counters of the updated sites.  COUNTS (black pass): *ne_total receives
+// the plane of colour COLOUR.  lane_hist: per-lane histogram counters of the
+// updated sites.  COUNTS (black pass): *ne_total receives
 // the number of unequal (site, neighbour) pairs after the update.
 template <int QB, int COLOUR, bool COUNTS, bool PAIRS, bool LT0,
           int LAY = kLayoutU8, int NW = 4>
@@ -414,6 +414,7 @@ __device__ __forceinline__ void walk_column(const PassArgs &A,
   load_words<LAY, NW>(w.oth_cur, false, w.Ce);
   load_words<LAY, NW>(w.own_cur, true, w.S);
   w.i = i0;
+  w.g0 = (uint32_t)(((int64_t)(i0 + A.grow0) * H + x0) >> 2);
   uint32_t ne_acc = 0;
   int32_t r = 0;
   // Side neighbour at x-1 when (lattice row + colour) is even.  Walks start
