@@ -16,6 +16,14 @@
 // bit (same words, same rule, same order of dependence: every white site
 // before any black site).  U8 layout, Metropolis rule, L a multiple of 1024
 // (the tile is 32 chunks = 512 sites of a plane row wide and 32 rows high).
+//
+// Tiles move by the copy engine (TMA): one warp issues a 1-D bulk copy
+// (cp.async.bulk) per tile row segment (a row splits into at most three
+// where the tile's halo wraps around the plane's ends) that completes on a
+// shared-memory mbarrier, and the interiors go back with bulk stores from
+// shared memory.  Every wait on the mbarrier is bounded: a CTA that gives up
+// flags the sweep's record (bit 63 of B, which no real count reaches) and
+// returns, and the host turns the flag into POTTS_ETIMEOUT.
 #include "internal.cuh"
 
 namespace potts {
@@ -33,6 +41,87 @@ constexpr int kFPairBins = 256;
 
 __device__ __forceinline__ int32_t fwrap(int32_t a, int32_t n) {
   return a < 0 ? a + n : (a >= n ? a - n : a);
+}
+
+// ------------------------------------------------------------ TMA helpers
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar),
+               "r"(count)
+               : "memory");
+  // make the initialised barrier visible to the copy engine
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile(
+      "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar),
+      "r"(bytes)
+      : "memory");
+}
+// Bulk copy of n bytes (multiple of 16, both addresses 16-byte aligned)
+// from global memory into this CTA's shared memory, completing on mbar.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src,
+                                          uint32_t n, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(n), "r"(mbar)
+      : "memory");
+}
+// Bulk store of n bytes from shared to global memory (bulk-group tracked).
+__device__ __forceinline__ void bulk_store(void *dst, uint32_t src,
+                                           uint32_t n) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::
+                   "l"(dst),
+               "r"(src), "r"(n)
+               : "memory");
+}
+// Waits for phase `parity` of mbar; gives up after `tries` polls (each
+// poll itself suspends for a bounded time).  Returns whether it completed.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity,
+                                          uint32_t tries) {
+  for (uint32_t i = 0; i < tries; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+constexpr uint32_t kWaitTries = 1u << 20;
+constexpr unsigned long long kTimeoutFlag = 1ull << 63;
+
+// Copies `rows` tile rows (halo `h` chunks on each side, tile width kFTW
+// chunks) of a plane into shared memory at `dst` (row stride `stride`):
+// lane `lane` of the issuing warp takes rows lane, lane + 32, ...; each row
+// is one to three contiguous segments (the halo wraps around the plane's
+// row ends).
+__device__ __forceinline__ void stage_rows(uint32_t dst, int32_t stride,
+                                           const uint8_t *plane, int32_t H,
+                                           int32_t L, int32_t row_first,
+                                           int32_t rows, int32_t c0, int32_t h,
+                                           uint32_t lane, uint32_t mbar) {
+  const int32_t nch = H / 16, width = kFTW + 2 * h;
+  for (int32_t rr = (int32_t)lane; rr < rows; rr += 32) {
+    const uint8_t *grow = plane + (int64_t)fwrap(row_first + rr, L) * H;
+    int32_t start = c0 - h, done = 0;
+    while (done < width) {
+      const int32_t gc = start < 0 ? start + nch : (start >= nch ? start - nch
+                                                                 : start);
+      const int32_t len = min(width - done, nch - gc);
+      bulk_load(dst + (uint32_t)(rr * stride + done * 16), grow + gc * 16,
+                (uint32_t)(len * 16), mbar);
+      done += len;
+      start += len;
+    }
+  }
 }
 
 __device__ __forceinline__ void lds4(const uint8_t *p, uint32_t w[4]) {
@@ -107,26 +196,32 @@ __global__ void __launch_bounds__(kFThreads, 3)
   for (uint32_t v = tid; v < bins * 32u; v += kFThreads) s_hist[v] = 0;
   if (tid < 16) s_fold[tid] = 0;
   if (tid == 0) s_sat = 0;
+  __shared__ __align__(8) unsigned long long s_mbar;
+  const uint32_t mbar = smem_addr(&s_mbar);
+  if (tid == 0) mbar_init(mbar, 1);
+  __syncthreads();
   pdl_wait_previous();  // the planes are the previous sweep's output
 
   const int32_t nch = H / 16;
   const int32_t c0 = (int32_t)blockIdx.x * kFTW;
   const int32_t r0 = (int32_t)blockIdx.y * kFR;
-  for (int32_t it = (int32_t)tid; it < kBRows * kBChunks; it += kFThreads) {
-    const int32_t rr = it / kBChunks, cc = it - rr * kBChunks;
-    const int32_t gi = fwrap(r0 - 2 + rr, L), gc = fwrap(c0 - 2 + cc, nch);
-    *reinterpret_cast<uint4 *>(sb + rr * kBStride + cc * 16) =
-        __ldg(reinterpret_cast<const uint4 *>(black + (int64_t)gi * H +
-                                              gc * 16));
+  if (tid < 32) {
+    // the whole tile pair: expected bytes first, then the copies
+    if (tid == 0) mbar_expect_tx(mbar, (uint32_t)(kBBytes + kWBytes));
+    __syncwarp();
+    stage_rows(smem_addr(sb), kBStride, black, H, L, r0 - 2, kBRows, c0, 2,
+               tid, mbar);
+    stage_rows(smem_addr(sw), kWStride, white, H, L, r0 - 1, kWRows, c0, 1,
+               tid, mbar);
   }
-  for (int32_t it = (int32_t)tid; it < kWRows * kWChunks; it += kFThreads) {
-    const int32_t rr = it / kWChunks, cc = it - rr * kWChunks;
-    const int32_t gi = fwrap(r0 - 1 + rr, L), gc = fwrap(c0 - 1 + cc, nch);
-    *reinterpret_cast<uint4 *>(sw + rr * kWStride + cc * 16) =
-        __ldg(reinterpret_cast<const uint4 *>(white + (int64_t)gi * H +
-                                              gc * 16));
+  // every thread polls; the CTA gives up as a whole if any of them did
+  const bool landed = mbar_wait(mbar, 0, kWaitTries);
+  if (__syncthreads_or(!landed)) {
+    if (tid == 0) atomicOr(rec, kTimeoutFlag);
+    if (!landed) mbar_wait(mbar, 0, kWaitTries);  // copies in flight land
+    return;
   }
-  __syncthreads();
+  (void)nch;
 
   const PhiloxKey ks = philox_schedule(key0, key1);
   const uint8_t *tab = reinterpret_cast<const uint8_t *>(s_tab);
@@ -182,17 +277,20 @@ __global__ void __launch_bounds__(kFThreads, 3)
     for (int k = 0; k < 4; ++k) hist_word<PAIRS>(lh, N[k]);
   }
   pdl_release_next();
+  // the threads' shared-memory writes, visible to the copy engine
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
-  // both interiors to the output planes
-  for (int32_t it = (int32_t)tid; it < kFR * kFTW; it += kFThreads) {
-    const int32_t rr = it / kFTW, cc = it - rr * kFTW;
-    const int64_t g = (int64_t)(r0 + rr) * H + (c0 + cc) * 16;
-    __stcs(reinterpret_cast<uint4 *>(white_out + g),
-           *reinterpret_cast<const uint4 *>(sw + (rr + 1) * kWStride +
-                                            (cc + 1) * 16));
-    __stcs(reinterpret_cast<uint4 *>(black_out + g),
-           *reinterpret_cast<const uint4 *>(sb + (rr + 2) * kBStride +
-                                            (cc + 2) * 16));
+  // both interiors to the output planes: one bulk store per tile row and
+  // plane from shared memory (each interior row is contiguous on both sides)
+  if (tid < 32) {
+    for (int32_t rr = (int32_t)tid; rr < kFR; rr += 32) {
+      const int64_t g = (int64_t)(r0 + rr) * H + c0 * 16;
+      bulk_store(white_out + g, smem_addr(sw + (rr + 1) * kWStride + 16),
+                 kFTW * 16);
+      bulk_store(black_out + g, smem_addr(sb + (rr + 2) * kBStride + 32),
+                 kFTW * 16);
+    }
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
   }
   // B of the black interior (each bond has one black end), then the counts
   uint32_t sat = 64u * items - ne;
@@ -222,6 +320,8 @@ __global__ void __launch_bounds__(kFThreads, 3)
       if (sum) atomicAdd(rec + 1 + v, (unsigned long long)sum);
     }
   }
+  // the tiles must stay until the bulk stores have read them
+  if (tid < 32) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 // Largest dynamic shared memory of any launch: both tiles and 256 x 32

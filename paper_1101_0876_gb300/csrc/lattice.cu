@@ -307,6 +307,11 @@ int potts_sweep(potts_h h, double beta, int64_t nsweeps, uint64_t *out_counts) {
     POTTS_CK(cudaMemcpyAsync(h->h_rec, h->d_rec, (size_t)(n * rec_len * 8),
                              cudaMemcpyDeviceToHost, h->stream));
     POTTS_CK(cudaStreamSynchronize(h->stream));
+    // the fused sweep marks B's top bit when a tile copy did not complete
+    for (int64_t s = 0; s < n; ++s)
+      if (h->h_rec[s * rec_len] >> 63)
+        return fail(POTTS_ETIMEOUT, "sweep %llu: a tile copy of the fused "
+                    "sweep did not complete", (unsigned long long)(h->sweep + s));
     for (int64_t s = 0; s < n; ++s)
       update_obs(&h->obs, h->h_rec + s * rec_len, h->L, q, true);
     if (out_counts)
