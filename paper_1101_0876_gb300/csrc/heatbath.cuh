@@ -128,13 +128,23 @@ __device__ __forceinline__ uint32_t hb_ge(uint32_t a, uint32_t b) {
   return (((a | 0x80808080u) - b) & 0x80808080u) >> 7;
 }
 
-// Bit FROM of every byte moved to bit TO.
+// The same with a | 0x80808080 given and the subtraction issued as a
+// multiply-add (b * neg + aM, neg = -1 at run time) on the FMA-heavy pipe.
+__device__ __forceinline__ uint32_t hb_ge_m(uint32_t aM, uint32_t b,
+                                            uint32_t neg) {
+  return ((b * neg + aM) & 0x80808080u) >> 7;
+}
+
+// Bit FROM of every byte moved to bit TO and added to acc (the fields are
+// disjoint, so the additions are ORs): a multiply-add for a left move, a
+// high multiply with an addend for a right move, both on the FMA-heavy pipe.
 template <int FROM, int TO>
-__device__ __forceinline__ uint32_t hb_mv(uint32_t x) {
-  if constexpr (FROM >= TO)
-    return x >> (FROM - TO);
+__device__ __forceinline__ uint32_t hb_put(uint32_t x, uint32_t acc,
+                                           uint32_t one) {
+  if constexpr (FROM > TO)
+    return __umulhi(x, 1u << (32 - (FROM - TO))) + acc;
   else
-    return x << (TO - FROM);
+    return x * (one << (TO - FROM)) + acc;
 }
 
 // The four sites of one word at once (spins < 2^QB, QB <= 6): the same
@@ -145,8 +155,12 @@ __device__ __forceinline__ uint32_t hb_mv(uint32_t x) {
 // idx + #{held d : d - rank(d) <= idx}).
 // U, D, Lw, Rw: neighbour words (up, down, left, right); uw: Philox words;
 // sW: the launch's table (hb_build_table).
-// one: the run-time 1 of PassArgs, so the six byte additions issue as
-// multiply-adds on the FMA-heavy pipe (the ALU pipe is the busy one here).
+// one: the run-time 1 of PassArgs.  The rule is mostly byte-SIMD ALU work,
+// so its additions, subtractions (x * neg + y with neg = -1 at run time) and
+// bit-field moves issue as multiply-adds on the FMA-heavy pipe, which this
+// pass otherwise leaves two thirds idle; every step is exact 32-bit
+// arithmetic whose per-byte results stay in 0..255, so the order of the
+// additions does not matter.
 template <int QB>
 __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
                                             uint32_t Lw, uint32_t Rw,
@@ -155,8 +169,9 @@ __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
                                             uint32_t one) {
   static_assert(QB <= 6, "byte sums below need spins < 64");
   constexpr uint32_t K = Swar<QB>::K, M = Swar<QB>::M;
-  constexpr uint32_t ONE = 0x01010101u;
+  constexpr uint32_t ONE = 0x01010101u, HI = 0x80808080u;
   constexpr uint32_t SENT = 0x7F7F7F7Fu;  // above every state < 64
+  const uint32_t neg = 0u - one;          // -1 at run time
   // 2^QB per byte where two neighbours are equal
   const uint32_t E01 = ~((U ^ D) * one + K) & M;
   const uint32_t E02 = ~((U ^ Lw) * one + K) & M;
@@ -165,9 +180,12 @@ __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
   const uint32_t E13 = ~((D ^ Rw) * one + K) & M;
   const uint32_t E23 = ~((Lw ^ Rw) * one + K) & M;
   // pattern code per byte (bit order of the table)
-  const uint32_t CODE = hb_mv<QB, 0>(E01) | hb_mv<QB, 1>(E02) |
-                        hb_mv<QB, 2>(E03) | hb_mv<QB, 3>(E12) |
-                        hb_mv<QB, 4>(E13) | hb_mv<QB, 5>(E23);
+  uint32_t CODE = hb_put<QB, 0>(E01, 0u, one);
+  CODE = hb_put<QB, 1>(E02, CODE, one);
+  CODE = hb_put<QB, 2>(E03, CODE, one);
+  CODE = hb_put<QB, 3>(E12, CODE, one);
+  CODE = hb_put<QB, 4>(E13, CODE, one);
+  CODE = hb_put<QB, 5>(E23, CODE, one);
   // first appearances (1 per byte) and their byte masks
   const uint32_t F1 = (E01 ^ M) >> QB;
   const uint32_t F2 = (~(E02 | E12) & M) >> QB;
@@ -177,12 +195,19 @@ __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
   const uint32_t H1 = (D & m1) | (SENT & ~m1);
   const uint32_t H2 = (Lw & m2) | (SENT & ~m2);
   const uint32_t H3 = (Rw & m3) | (SENT & ~m3);
-  const uint32_t g01 = hb_ge(U, H1), g02 = hb_ge(U, H2), g03 = hb_ge(U, H3);
-  const uint32_t g12 = hb_ge(H1, H2), g13 = hb_ge(H1, H3), g23 = hb_ge(H2, H3);
-  const uint32_t T0 = U - (g01 + g02 + g03);
-  const uint32_t T1 = H1 - ((g01 ^ ONE) + g12 + g13);
-  const uint32_t T2 = H2 - ((g02 ^ ONE) + (g12 ^ ONE) + g23);
-  const uint32_t T3 = H3 - ((g03 ^ ONE) + (g13 ^ ONE) + (g23 ^ ONE));
+  const uint32_t UM = U | HI, H1M = H1 | HI, H2M = H2 | HI;
+  const uint32_t g01 = hb_ge_m(UM, H1, neg), g02 = hb_ge_m(UM, H2, neg),
+                 g03 = hb_ge_m(UM, H3, neg);
+  const uint32_t g12 = hb_ge_m(H1M, H2, neg), g13 = hb_ge_m(H1M, H3, neg),
+                 g23 = hb_ge_m(H2M, H3, neg);
+  // T_i = held state i minus its rank among the held states
+  const uint32_t T0 = g03 * neg + (g02 * neg + (g01 * neg + U));
+  const uint32_t T1 =
+      g13 * neg + (g12 * neg + (g01 * one + (H1 * one + (0u - ONE))));
+  const uint32_t T2 =
+      g23 * neg + (g12 * one + (g02 * one + (H2 * one + (0u - 2u * ONE))));
+  const uint32_t T3 =
+      g23 * one + (g13 * one + (g03 * one + (H3 * one + (0u - 3u * ONE))));
   const uint8_t *ent = reinterpret_cast<const uint8_t *>(sW + 8);
   uint32_t idx[4], cls[4];
 #pragma unroll
@@ -191,24 +216,28 @@ __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
     const uint4 sb = *reinterpret_cast<const uint4 *>(ent + off);
     const uint32_t Z = *reinterpret_cast<const uint32_t *>(ent + off + 16);
     const uint32_t r = __umulhi(uw[b], Z);
-    idx[b] = min((r - sb.w) >> m, 0x40u);  // < q - k <= 62 when used
+    idx[b] = min((sb.w * neg + r) >> m, 0x40u);  // < q - k <= 62 when used
     cls[b] = (uint32_t)(r >= sb.x) + (uint32_t)(r >= sb.y) +
              (uint32_t)(r >= sb.z) + (uint32_t)(r >= sb.w);
   }
   const uint32_t IDX = pack4(idx[0], idx[1], idx[2], idx[3]);
   const uint32_t CLS = pack4(cls[0], cls[1], cls[2], cls[3]);
+  const uint32_t IDXM = IDX | HI;
   const uint32_t P =
-      IDX + hb_ge(IDX, T0) + hb_ge(IDX, T1) + hb_ge(IDX, T2) + hb_ge(IDX, T3);
-  // per byte: class 0..3 takes that neighbour, 4 the unheld state
-  auto is = [&](uint32_t c) {
+      hb_ge_m(IDXM, T3, neg) * one +
+      (hb_ge_m(IDXM, T2, neg) * one +
+       (hb_ge_m(IDXM, T1, neg) * one + (hb_ge_m(IDXM, T0, neg) * one + IDX)));
+  // per byte: class 0..3 takes that neighbour, 4 the unheld state; ne(c) is
+  // 0xFF where the class differs from c
+  auto ne = [&](uint32_t c) {
     const uint32_t x = CLS ^ (c * ONE);  // 0 where equal, bytes < 8
-    return ((((x + 0x7F7F7F7Fu) | x) & 0x80808080u) >> 7) * 0xFFu ^ 0xFFFFFFFFu;
+    return ((((x * one + 0x7F7F7F7Fu) | x) & HI) >> 7) * 0xFFu;
   };
   uint32_t N = P;
-  N = (U & is(0u)) | (N & ~is(0u));
-  N = (D & is(1u)) | (N & ~is(1u));
-  N = (Lw & is(2u)) | (N & ~is(2u));
-  N = (Rw & is(3u)) | (N & ~is(3u));
+  N = (N & ne(0u)) | (U & ~ne(0u));
+  N = (N & ne(1u)) | (D & ~ne(1u));
+  N = (N & ne(2u)) | (Lw & ~ne(2u));
+  N = (N & ne(3u)) | (Rw & ~ne(3u));
   return N;
 }
 
