@@ -285,9 +285,10 @@ int potts_strip_rows(potts_h h, int32_t colour, void **rows,
  * rows, queued on the strip's stream.  The halo rows of plane 1 - colour
  * must hold the neighbours' rows as they stand after the neighbours' latest
  * pass of colour 1 - colour.  d_record: device memory of 1 + q uint64 the
- * strip's partial counts are added to (the histogram of its updated sites,
- * and on the black pass the satisfied bonds of its black sites); the caller
- * zeroes it per sweep and sums it over the strips.  Passes alternate white
+ * strip's partial counts are added to (the histogram of its sites and the
+ * satisfied bonds of its black sites, complete after the black pass: how
+ * the histogram is split between the two passes depends on q and the row
+ * width); the caller zeroes it per sweep and sums it over the strips.  Passes alternate white
  * (0), black (1); the black pass advances the strip's sweep index.  Does
  * not synchronise.  Errors: EINVAL (not a strip, colour, beta as for
  * potts_sweep), ECUDA. */

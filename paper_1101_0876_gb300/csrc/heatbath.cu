@@ -20,19 +20,23 @@ constexpr int kHbPairBins = 256;
 #define POTTS_HB_MINB 3
 #endif
 
-// Same grid, walk and reductions as the Metropolis pass kernel.
-template <int QB, int COLOUR, bool PAIRS, int LAY>
+// Same grid, walk and reductions as the Metropolis pass kernel (XP: the
+// histogram of both planes in (black, white) pair bins, black pass only).
+template <int QB, int COLOUR, bool PAIRS, int LAY, bool XP = false>
 __global__ void __launch_bounds__(kPassThreads, QB <= 6 ? 4 : POTTS_HB_MINB)
     hb_pass_kernel(PassArgs A, HeatTable T, TileGeom G,
                    unsigned long long *rec) {
   constexpr bool COUNTS = COLOUR == 1;
+  constexpr bool HIST = !XP || COUNTS;
+  constexpr bool PBINS = PAIRS || XP;
   extern __shared__ uint32_t s_hist[];
   __shared__ __align__(16) uint32_t s_W[kHbTableWords];
   __shared__ uint32_t s_sat;
   __shared__ uint32_t s_fold[16];
   const uint32_t tid = threadIdx.x;
-  const uint32_t bins = PAIRS ? (uint32_t)kHbPairBins : A.hist_bins;
-  for (uint32_t v = tid; v < bins * 32u; v += kPassThreads) s_hist[v] = 0;
+  const uint32_t bins = PBINS ? (uint32_t)kHbPairBins : A.hist_bins;
+  if (HIST)
+    for (uint32_t v = tid; v < bins * 32u; v += kPassThreads) s_hist[v] = 0;
   if (tid < 16) s_fold[tid] = 0;
   if (tid == 0) s_sat = 0;
   hb_build_table(s_W, T.W, A.q, T.m, tid);  // ends with a barrier
@@ -47,7 +51,7 @@ __global__ void __launch_bounds__(kPassThreads, QB <= 6 ? 4 : POTTS_HB_MINB)
       const int32_t i0 = A.row_lo + (tile * G.RG + rg) * G.TR;
       if (i0 >= A.row_end) continue;
       const int32_t rows = min(G.TR, A.row_end - i0);
-      hb_walk_column<QB, COLOUR, COUNTS, PAIRS, LAY>(
+      hb_walk_column<QB, COLOUR, COUNTS, PAIRS, LAY, XP>(
           A, ks, s_W, T.m, chunk * 16, i0, rows, s_hist + (tid & 31u), &ne);
       rows_done += (uint32_t)rows;
     }
@@ -61,7 +65,8 @@ __global__ void __launch_bounds__(kPassThreads, QB <= 6 ? 4 : POTTS_HB_MINB)
   }
   __syncthreads();
   if (COUNTS && tid == 0 && s_sat) atomicAdd(rec, (unsigned long long)s_sat);
-  if (PAIRS) {
+  if (!HIST) return;
+  if (PBINS) {
     for (uint32_t p = tid; p < (uint32_t)kHbPairBins; p += kPassThreads) {
       uint32_t sum = 0;
 #pragma unroll 8
@@ -84,14 +89,14 @@ __global__ void __launch_bounds__(kPassThreads, QB <= 6 ? 4 : POTTS_HB_MINB)
   }
 }
 
-template <int QB, int COLOUR, bool PAIRS, int LAY>
+template <int QB, int COLOUR, bool PAIRS, int LAY, bool XP = false>
 cudaError_t launch_hb_c(const PassArgs &A, const HeatTable &T,
                         const TileGeom &G, unsigned long long *rec,
                         cudaStream_t st) {
   dim3 grid(G.gx, G.gy), block(kPassThreads);
-  const size_t smem =
-      (size_t)(PAIRS ? kHbPairBins : A.hist_bins) * 32u * sizeof(uint32_t);
-  return launch_pdl(hb_pass_kernel<QB, COLOUR, PAIRS, LAY>, grid, block,
+  const size_t bins = (PAIRS || XP) ? kHbPairBins : A.hist_bins;
+  const size_t smem = (XP && COLOUR == 0) ? 0 : bins * 32u * sizeof(uint32_t);
+  return launch_pdl(hb_pass_kernel<QB, COLOUR, PAIRS, LAY, XP>, grid, block,
                     smem, st, A, T, G, rec);
 }
 
@@ -100,6 +105,9 @@ cudaError_t launch_hb_lay(const PassArgs &A, const HeatTable &T,
                           const TileGeom &G, unsigned long long *rec,
                           cudaStream_t st) {
   if constexpr (QB == 4) {
+    if (G.pairs == 2)
+      return A.colour ? launch_hb_c<4, 1, false, LAY, true>(A, T, G, rec, st)
+                      : launch_hb_c<4, 0, false, LAY, true>(A, T, G, rec, st);
     if (G.pairs)
       return A.colour ? launch_hb_c<4, 1, true, LAY>(A, T, G, rec, st)
                       : launch_hb_c<4, 0, true, LAY>(A, T, G, rec, st);

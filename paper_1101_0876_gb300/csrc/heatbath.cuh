@@ -242,8 +242,9 @@ __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
 }
 
 // One row of 16 sites (the Metropolis do_row with the heat-bath rule).
-// QB <= 6: the word rule; QB 8: the per-site rule (any q <= 256).
-template <int QB, bool LEFT, bool COUNTS, bool PAIRS, int LAY>
+// QB <= 6: the word rule; QB 8: the per-site rule (any q <= 256).  XP: the
+// cross-plane pair histogram (hist_cross, black pass only).
+template <int QB, bool LEFT, bool COUNTS, bool PAIRS, int LAY, bool XP = false>
 __device__ __forceinline__ void hb_row(const PassArgs &A, const PhiloxKey &ks,
                                        const uint32_t *sW, uint32_t m,
                                        Walk &w, int32_t x0, int32_t xb,
@@ -302,8 +303,15 @@ __device__ __forceinline__ void hb_row(const PassArgs &A, const PhiloxKey &ks,
     }
   }
   IO::store(w.own_cur, Nw);
+  if constexpr (XP) {
+    if (COUNTS) {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) hist_word<PAIRS>(lane_hist, Nw[k]);
+      for (int k = 0; k < 4; ++k) hist_cross(lane_hist, Nw[k], Cw[k]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) hist_word<PAIRS>(lane_hist, Nw[k]);
+  }
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     w.Up[k] = w.Ce[k];
@@ -317,7 +325,7 @@ __device__ __forceinline__ void hb_row(const PassArgs &A, const PhiloxKey &ks,
 }
 
 // walk_column with the heat-bath rule.
-template <int QB, int COLOUR, bool COUNTS, bool PAIRS, int LAY>
+template <int QB, int COLOUR, bool COUNTS, bool PAIRS, int LAY, bool XP = false>
 __device__ __forceinline__ void hb_walk_column(
     const PassArgs &A, const PhiloxKey &ks, const uint32_t *sW, uint32_t m,
     int32_t x0, int32_t i0, int32_t rows, uint32_t *lane_hist,
@@ -341,9 +349,9 @@ __device__ __forceinline__ void hb_walk_column(
   int32_t r = 0;
   if (((i0 + A.grow0) & 1) == 0) {
     for (; r + 2 <= rows; r += 2) {
-      hb_row<QB, COLOUR == 0, COUNTS, PAIRS, LAY>(
+      hb_row<QB, COLOUR == 0, COUNTS, PAIRS, LAY, XP>(
           A, ks, sW, m, w, x0, xb, xl, xr, RB, true, lane_hist, ne_acc);
-      hb_row<QB, COLOUR == 1, COUNTS, PAIRS, LAY>(
+      hb_row<QB, COLOUR == 1, COUNTS, PAIRS, LAY, XP>(
           A, ks, sW, m, w, x0, xb, xl, xr, RB, r + 2 < rows, lane_hist,
           ne_acc);
       if (COUNTS) {
@@ -355,10 +363,10 @@ __device__ __forceinline__ void hb_walk_column(
   for (; r < rows; ++r) {
     const bool left = ((w.i + A.grow0 + COLOUR) & 1) == 0;
     if (left)
-      hb_row<QB, true, COUNTS, PAIRS, LAY>(A, ks, sW, m, w, x0, xb, xl, xr,
+      hb_row<QB, true, COUNTS, PAIRS, LAY, XP>(A, ks, sW, m, w, x0, xb, xl, xr,
                                            RB, r + 1 < rows, lane_hist, ne_acc);
     else
-      hb_row<QB, false, COUNTS, PAIRS, LAY>(A, ks, sW, m, w, x0, xb, xl, xr,
+      hb_row<QB, false, COUNTS, PAIRS, LAY, XP>(A, ks, sW, m, w, x0, xb, xl, xr,
                                             RB, r + 1 < rows, lane_hist,
                                             ne_acc);
     if (COUNTS) {

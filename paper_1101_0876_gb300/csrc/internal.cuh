@@ -54,7 +54,9 @@ class DeviceScope {
 struct TileGeom {
   int32_t CX, RG, TR;
   int32_t gx, gy, ty;
-  int32_t pairs;  // histogram bins are (state, state) pairs (q <= 16)
+  int32_t pairs;  // q <= 16: 1, bins of (state, state) pairs of one plane;
+                  // 2 (32-site U8 pass), (black, white) pairs of the two
+                  // planes kept by the black pass alone; 0: one state a bin
   int32_t sites;  // sites per thread and row: 16, or 32 (U8 Metropolis)
   int32_t nibble; // 1: the U4 Metropolis pass on nibbles (pass_u4.cuh)
 };
@@ -125,8 +127,11 @@ HeatTable heat_table(const uint64_t W[5], int32_t m);
 
 // ----------------------------------------------------------- launches
 // One colour pass of one lattice.  rec (not null) receives, added
-// atomically, the histogram of the updated sites and, on the black pass, B;
-// the record {B, hist[q]} of a sweep must start at zero.
+// atomically, histogram counts and, on the black pass, B; the record
+// {B, hist[q]} of a sweep must start at zero and is complete after the
+// black pass.  Each pass counts its updated sites, except with G.pairs == 2,
+// where the black pass counts the sites of both planes and the white pass
+// none.
 cudaError_t launch_pass(const PassArgs &A, const AcceptTable &T,
                         const TileGeom &G, unsigned long long *rec,
                         cudaStream_t st);

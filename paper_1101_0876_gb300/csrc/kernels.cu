@@ -25,21 +25,27 @@ constexpr int kPairBins = 256;
 // per-row work), and 128 for the nibble pass.
 constexpr int kMinb32 = 3, kMinbNib = 4;
 
-template <int QB, int COLOUR, bool PAIRS, bool LT0, int LAY, int NW>
+// XP (q <= 16): the histogram of both planes in (black, white) pair bins,
+// kept by the black pass alone (hist_cross); the white pass keeps none.
+template <int QB, int COLOUR, bool PAIRS, bool LT0, int LAY, int NW,
+          bool XP = false>
 __global__ void __launch_bounds__(kPassThreads,
                                   NW == 8 ? kMinb32 : POTTS_PASS_MINB)
     pass_kernel(PassArgs A, AcceptTable Tin, TileGeom G,
                 unsigned long long *rec) {
   constexpr bool COUNTS = COLOUR == 1;
+  constexpr bool HIST = !XP || COUNTS;     // this pass keeps a histogram
+  constexpr bool PBINS = PAIRS || XP;      // 256 pair bins, folded at the end
   extern __shared__ uint32_t s_hist[];  // bins * 32 (bins = 256 or q)
   __shared__ __align__(16) uint32_t s_tab[kTabWords];
   __shared__ uint32_t s_sat;
   __shared__ uint32_t s_fold[16];
   const uint32_t tid = threadIdx.x;
-  const uint32_t bins = PAIRS ? (uint32_t)kPairBins : A.hist_bins;
+  const uint32_t bins = PBINS ? (uint32_t)kPairBins : A.hist_bins;
   for (uint32_t i = tid; i < (uint32_t)kTabWords; i += kPassThreads)
     s_tab[i] = (i % 4u == 0 && i / 4u < 9u) ? Tin.tab[i / 4u] : 0u;
-  for (uint32_t v = tid; v < bins * 32u; v += kPassThreads) s_hist[v] = 0;
+  if (HIST)
+    for (uint32_t v = tid; v < bins * 32u; v += kPassThreads) s_hist[v] = 0;
   if (tid < 16) s_fold[tid] = 0;
   if (tid == 0) s_sat = 0;
   __syncthreads();
@@ -54,7 +60,7 @@ __global__ void __launch_bounds__(kPassThreads,
       const int32_t i0 = A.row_lo + (tile * G.RG + rg) * G.TR;
       if (i0 >= A.row_end) continue;
       const int32_t rows = min(G.TR, A.row_end - i0);
-      walk_column<QB, COLOUR, COUNTS, PAIRS, LT0, LAY, NW>(
+      walk_column<QB, COLOUR, COUNTS, PAIRS, LT0, LAY, NW, XP>(
           A, ks, reinterpret_cast<const uint8_t *>(s_tab), chunk * 4 * NW, i0,
           rows, s_hist + (tid & 31u), &ne);
       rows_done += (uint32_t)rows;
@@ -69,7 +75,8 @@ __global__ void __launch_bounds__(kPassThreads,
   }
   __syncthreads();
   if (COUNTS && tid == 0 && s_sat) atomicAdd(rec, (unsigned long long)s_sat);
-  if (PAIRS) {
+  if (!HIST) return;
+  if (PBINS) {
     // fold pair bins (v0 | v1 << 4) back to the 16 states
     for (uint32_t p = tid; p < (uint32_t)kPairBins; p += kPassThreads) {
       uint32_t sum = 0;
@@ -152,17 +159,19 @@ __global__ void __launch_bounds__(kPassThreads, kMinbNib)
     atomicAdd(rec + 1 + tid, (unsigned long long)s_fold[tid]);
 }
 
-template <int QB, int COLOUR, bool PAIRS, int LAY = kLayoutU8, int NW = 4>
+template <int QB, int COLOUR, bool PAIRS, int LAY = kLayoutU8, int NW = 4,
+          bool XP = false>
 static cudaError_t launch_c(const PassArgs &A, const AcceptTable &T,
                             const TileGeom &G, unsigned long long *rec,
                             cudaStream_t st) {
   dim3 grid(G.gx, G.gy), block(kPassThreads);
+  const size_t bins = (PAIRS || XP) ? kPairBins : A.hist_bins;
   const size_t smem =
-      (size_t)(PAIRS ? kPairBins : A.hist_bins) * 32u * sizeof(uint32_t);
+      (XP && COLOUR == 0) ? 0 : bins * 32u * sizeof(uint32_t);
   if (T.rule_lt0)
-    return launch_pdl(pass_kernel<QB, COLOUR, PAIRS, true, LAY, NW>, grid,
+    return launch_pdl(pass_kernel<QB, COLOUR, PAIRS, true, LAY, NW, XP>, grid,
                       block, smem, st, A, T, G, rec);
-  return launch_pdl(pass_kernel<QB, COLOUR, PAIRS, false, LAY, NW>, grid,
+  return launch_pdl(pass_kernel<QB, COLOUR, PAIRS, false, LAY, NW, XP>, grid,
                     block, smem, st, A, T, G, rec);
 }
 
@@ -170,6 +179,12 @@ template <int QB>
 static cudaError_t launch_qb(const PassArgs &A, const AcceptTable &T,
                              const TileGeom &G, unsigned long long *rec,
                              cudaStream_t st) {
+  if constexpr (QB == 4) {
+    if (G.sites == 32 && G.pairs == 2)
+      return A.colour
+                 ? launch_c<QB, 1, false, kLayoutU8, 8, true>(A, T, G, rec, st)
+                 : launch_c<QB, 0, false, kLayoutU8, 8, true>(A, T, G, rec, st);
+  }
   if (G.sites == 32)
     return A.colour ? launch_c<QB, 1, false, kLayoutU8, 8>(A, T, G, rec, st)
                     : launch_c<QB, 0, false, kLayoutU8, 8>(A, T, G, rec, st);
@@ -278,8 +293,12 @@ TileGeom choose_geom(int32_t L, int32_t H, int32_t q, int32_t sm_count,
 
 TileGeom pass_geom(int32_t nrows, int32_t H, int32_t q, int32_t layout,
                    int32_t update, int32_t sm_count) {
-  if (update == POTTS_UPDATE_HEATBATH)
-    return choose_geom(nrows, H, q, sm_count, 0);
+  if (update == POTTS_UPDATE_HEATBATH) {
+    // q <= 16: the histogram in (black, white) pair bins, black pass only
+    TileGeom g = choose_geom(nrows, H, q, sm_count, 0);
+    if (q <= 16) g.pairs = 2;
+    return g;
+  }
   if (layout == kLayoutU4) {
     TileGeom g = choose_geom(nrows, H, q, sm_count, 0, 16, kMinbNib);
     g.pairs = 1;
@@ -289,10 +308,11 @@ TileGeom pass_geom(int32_t nrows, int32_t H, int32_t q, int32_t layout,
   if (H % 32 == 0 && q <= 16) {
     // 32 sites per thread for the cheap q <= 16 rule (1.205 against 1.232
     // ps per update at L = 32768, q = 9; at q = 96 the longer rows are 0.7 %
-    // slower), one state per bin: there the pair bins' 32 KB of shared
-    // memory per CTA buy nothing (1.2102 against 1.2076 ps)
+    // slower); the histogram in (black, white) pair bins on the black pass
+    // alone (pairs of one plane's neighbouring sites bought nothing here:
+    // 1.2102 against 1.2076 ps with one state per bin)
     TileGeom g = choose_geom(nrows, H, q, sm_count, 0, 32, kMinb32);
-    g.pairs = 0;
+    g.pairs = 2;
     return g;
   }
   return choose_geom(nrows, H, q, sm_count, 0);

@@ -207,6 +207,21 @@ __device__ __forceinline__ void hist_word(uint32_t *lane_hist, uint32_t w) {
   }
 }
 
+// Histogram of one black word's new spins paired with the white spins at
+// the same plane position (q <= 16): byte b of nw + (cw << 4) is the bin
+// (black spin, white spin), so four shared atomics count eight sites and
+// the white pass keeps no histogram.  The white plane is final when the
+// black pass runs, and the black walks read every white word of their rows
+// exactly once as the centre row.  Bytes above 15 (planes the caller did
+// not check) can only scramble the bins, never leave them.
+__device__ __forceinline__ void hist_cross(uint32_t *lane_hist, uint32_t nw,
+                                           uint32_t cw) {
+  const uint32_t t = nw + (cw << 4);
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+    atomicAdd(lane_hist + __byte_perm(t, 0u, 0x4440u + (uint32_t)b) * 32u, 1u);
+}
+
 // ------------------------------------------------------- plane layouts
 // U8: one byte per spin, 16 sites = 16 bytes per thread-row.
 // U4: two spins per byte (site 2b in the low nibble of byte b, site 2b+1 in
@@ -309,9 +324,10 @@ using Walk = WalkT<4>;
 // is at x-1 (row parity + colour even), else at x+1.  xb: byte offset of
 // the window in a row; xl, xr: byte offsets of the words holding the side
 // sites; RB: bytes per plane row; lane_hist: the lane's histogram counters
-// (not null).
+// (not null).  XP: the cross-plane pair histogram (hist_cross) instead of
+// one of the updated sites per pass.
 template <int QB, bool LEFT, bool COUNTS, bool PAIRS, bool LT0, int LAY,
-          int NW = 4>
+          int NW = 4, bool XP = false>
 __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
                                        const uint8_t *tab, WalkT<NW> &w,
                                        int32_t x0, int32_t xb, int32_t xl,
@@ -368,8 +384,15 @@ __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
     }
   }
   store_words<LAY, NW>(w.own_cur, Nw);
+  if constexpr (XP) {
+    if (COUNTS) {
 #pragma unroll
-  for (int k = 0; k < NW; ++k) hist_word<PAIRS>(lane_hist, Nw[k]);
+      for (int k = 0; k < NW; ++k) hist_cross(lane_hist, Nw[k], Cw[k]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NW; ++k) hist_word<PAIRS>(lane_hist, Nw[k]);
+  }
   // advance
 #pragma unroll
   for (int k = 0; k < NW; ++k) {
@@ -387,10 +410,11 @@ __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
 
 // Walks rows [i0, i0 + rows) of the 4 NW-site column starting at site x0 of
 // the plane of colour COLOUR.  lane_hist: per-lane histogram counters of the
-// updated sites.  COUNTS (black pass): *ne_total receives
+// updated sites (XP: of both planes' sites in pairs, on the black pass
+// only).  COUNTS (black pass): *ne_total receives
 // the number of unequal (site, neighbour) pairs after the update.
 template <int QB, int COLOUR, bool COUNTS, bool PAIRS, bool LT0,
-          int LAY = kLayoutU8, int NW = 4>
+          int LAY = kLayoutU8, int NW = 4, bool XP = false>
 __device__ __forceinline__ void walk_column(const PassArgs &A,
                                             const PhiloxKey &ks,
                                             const uint8_t *tab, int32_t x0,
@@ -431,10 +455,10 @@ __device__ __forceinline__ void walk_column(const PassArgs &A,
   };
   if (((i0 + A.grow0) & 1) == 0) {
     for (; r + 2 <= rows; r += 2) {
-      do_row<QB, COLOUR == 0, COUNTS, PAIRS, LT0, LAY, NW>(
+      do_row<QB, COLOUR == 0, COUNTS, PAIRS, LT0, LAY, NW, XP>(
           A, ks, tab, w, x0, xb, xl, xr, RB, true, lane_hist, ne_acc);
       if (NW > 4) fold();
-      do_row<QB, COLOUR == 1, COUNTS, PAIRS, LT0, LAY, NW>(
+      do_row<QB, COLOUR == 1, COUNTS, PAIRS, LT0, LAY, NW, XP>(
           A, ks, tab, w, x0, xb, xl, xr, RB, r + 2 < rows, lane_hist, ne_acc);
       fold();
     }
@@ -442,10 +466,10 @@ __device__ __forceinline__ void walk_column(const PassArgs &A,
   for (; r < rows; ++r) {
     const bool left = ((w.i + A.grow0 + COLOUR) & 1) == 0;
     if (left)
-      do_row<QB, true, COUNTS, PAIRS, LT0, LAY, NW>(
+      do_row<QB, true, COUNTS, PAIRS, LT0, LAY, NW, XP>(
           A, ks, tab, w, x0, xb, xl, xr, RB, r + 1 < rows, lane_hist, ne_acc);
     else
-      do_row<QB, false, COUNTS, PAIRS, LT0, LAY, NW>(
+      do_row<QB, false, COUNTS, PAIRS, LT0, LAY, NW, XP>(
           A, ks, tab, w, x0, xb, xl, xr, RB, r + 1 < rows, lane_hist, ne_acc);
     fold();
   }
