@@ -221,13 +221,16 @@ static void neighbours(const uint8_t *s, int32_t L, int32_t i, int32_t j,
 }
 
 /* The single-site heat-bath rule.  nb[0..3] are the neighbours (up, down,
- * left, right), u the site's 32-bit word.  The q states are laid out on
- * [0, Z): first the distinct neighbour states in the order they first
- * appear in nb, each with width W[count], then the states no neighbour
- * holds, in increasing order, each with width W[0] = 2^m.  The new spin is
- * the state whose interval holds r = floor(u Z / 2^32).  Returns it and
- * stores the change of B (neighbours equal to the new spin minus those
- * equal to the old one) in *dB. */
+ * left, right), u the site's 32-bit word.  State x has weight W[n_x]
+ * (n_x = neighbours in state x), written as the base W[0] = 2^m plus the
+ * excess W[n_x] - W[0], which is zero for a state no neighbour holds.
+ * [0, Z) is laid out as: first the excesses of the distinct neighbour
+ * states, in the order they first appear in nb, then q intervals of width
+ * 2^m, one per state in increasing order.  The new spin is the state whose
+ * interval holds r = floor(u Z / 2^32), so state x is drawn with
+ * probability W[n_x] / Z.  Returns it and stores the change of B
+ * (neighbours equal to the new spin minus those equal to the old one) in
+ * *dB. */
 static int heatbath_rule(int old, const int nb[4], uint32_t u, int32_t q,
                          const uint64_t W[5], int32_t m, int *dB) {
   int cls[4], cnt[4], k = 0;
@@ -243,28 +246,18 @@ static int heatbath_rule(int old, const int nb[4], uint32_t u, int32_t q,
       k += 1;
     }
   }
-  uint64_t Z = (uint64_t)(q - k) * W[0];
-  for (int b = 0; b < k; ++b) Z += W[cnt[b]];
+  uint64_t Z = (uint64_t)q * W[0];
+  for (int b = 0; b < k; ++b) Z += W[cnt[b]] - W[0];
   uint64_t r = ((uint64_t)u * Z) >> 32;
   int now = -1;
   for (int b = 0; b < k && now < 0; ++b) {
-    if (r < W[cnt[b]])
+    const uint64_t excess = W[cnt[b]] - W[0];
+    if (r < excess)
       now = cls[b];
     else
-      r -= W[cnt[b]];
+      r -= excess;
   }
-  if (now < 0) {
-    uint64_t idx = r >> m;  /* which of the q - k unheld states */
-    for (int x = 0; x < q && now < 0; ++x) {
-      int held = 0;
-      for (int a = 0; a < 4; ++a) held |= nb[a] == x;
-      if (held) continue;
-      if (idx == 0)
-        now = x;
-      else
-        idx -= 1;
-    }
-  }
+  if (now < 0) now = (int)(r >> m);  /* r < q 2^m here: one of the q bases */
   int n_old = 0, n_now = 0;
   for (int a = 0; a < 4; ++a) {
     n_old += nb[a] == old;

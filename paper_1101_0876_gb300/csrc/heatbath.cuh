@@ -6,11 +6,13 @@
 // Rule.  Given its four neighbours (up, down, left, right), a site takes
 // state x with probability W[n_x] / Z, n_x = number of neighbours in state
 // x, W[n] = round(2^m exp(beta n)) (W[0] = 2^m exactly), Z = sum over the q
-// states.  The states are laid out on [0, Z): first the distinct neighbour
-// states in the order they first appear in (up, down, left, right), each of
-// width W[count], then the states no neighbour holds, in increasing order,
-// each of width 2^m; the new spin is the state whose interval holds
-// r = floor(u Z / 2^32), u the site's Philox word.  The host picks m so that
+// states.  Each weight is the base 2^m plus the excess W[n_x] - W[0] (zero
+// for a state no neighbour holds), and [0, Z) is laid out as: first the
+// excesses of the distinct neighbour states in the order they first appear
+// in (up, down, left, right), then q intervals of width 2^m, one per state
+// in increasing order.  The new spin is the state whose interval holds
+// r = floor(u Z / 2^32), u the site's Philox word: a neighbour's state when
+// r falls in its excess, else (r - excesses) >> m.  The host picks m so that
 // Z < 2^32 for every neighbour configuration, so all of it is 32-bit.
 #pragma once
 #include <cstdint>
@@ -19,8 +21,7 @@
 
 namespace potts {
 
-// W[0..4] as above, W[5..7] = 0: the index of a neighbour that repeats an
-// earlier one, so its class has no width of its own.
+// W[0..4] as above (W[5..7] zero, unused).
 struct HeatTable {
   uint32_t W[8];
   uint32_t m;
@@ -30,10 +31,12 @@ struct HeatTable {
 // equality pattern of the four neighbours.  The pattern code of a site has
 // bit 0..5 = [up == down], [up == left], [up == right], [down == left],
 // [down == right], [left == right]; the interval bounds s1..s4 (cumulative
-// widths of the neighbour classes in first-appearance order) and the
-// normaliser Z depend on the site only through that code (and on W, q, m,
-// which are fixed for a launch).  Entry: {s1, s2, s3, s4, Z, 0, 0, 0}.  Of
-// the 64 codes only the 15 that are transitive occur.
+// excesses of the neighbours' states, a neighbour that repeats an earlier
+// one adding nothing) and the normaliser Z depend on the site only through
+// that code (and on W, q, m, which are fixed for a launch).  Entry:
+// {s1, s2, s3, s4, Z, 0, 0, 0}; r < s1 selects the up neighbour's state,
+// s1 <= r < s2 the down one's, and so on, r >= s4 the state (r - s4) >> m.
+// Of the 64 codes only the 15 that are transitive occur.
 constexpr int kHbTableWords = 8 + 64 * 8;
 
 // Fills entry `code` from W (sW[0..7], already in shared memory).
@@ -48,15 +51,16 @@ __device__ __forceinline__ void hb_pattern_entry(uint32_t *sW, uint32_t code,
   const uint32_t c1 = f1 ? 1u + e12 + e13 : 5u;
   const uint32_t c2 = f2 ? 1u + e23 : 5u;
   const uint32_t c3 = f3 ? 1u : 5u;
-  const uint32_t s1 = sW[c0], s2 = s1 + sW[c1], s3 = s2 + sW[c2],
-                 s4 = s3 + sW[c3];
-  const uint32_t k = 1u + f1 + f2 + f3;  // distinct neighbour states
+  // excess of a class of c equal neighbours (c = 5: a repeat, none)
+  auto ex = [&](uint32_t c) { return c <= 4u ? sW[c] - sW[0] : 0u; };
+  const uint32_t s1 = ex(c0), s2 = s1 + ex(c1), s3 = s2 + ex(c2),
+                 s4 = s3 + ex(c3);
   uint32_t *e = sW + 8 + 8 * code;
   e[0] = s1;
   e[1] = s2;
   e[2] = s3;
   e[3] = s4;
-  e[4] = s4 + ((q - k) << m);  // the unheld states, 2^m each
+  e[4] = s4 + (q << m);  // the q bases, 2^m each
   e[5] = e[6] = e[7] = 0u;
 }
 
@@ -71,49 +75,23 @@ __device__ __forceinline__ void hb_build_table(uint32_t *sW, const uint32_t *W,
   __syncthreads();
 }
 
-__device__ __forceinline__ void hb_cswap(uint32_t &a, uint32_t &b) {
-  const uint32_t lo = min(a, b), hi = max(a, b);
-  a = lo;
-  b = hi;
-}
-
 // New spin of one site.  t0..t3: neighbours (up, down, left, right); u: the
 // site's word; sW: the table in shared memory.
 __device__ __forceinline__ uint32_t hb_site(uint32_t t0, uint32_t t1,
                                             uint32_t t2, uint32_t t3,
                                             uint32_t u, uint32_t q,
                                             const uint32_t *sW, uint32_t m) {
-  const uint32_t e01 = t0 == t1, e02 = t0 == t2, e03 = t0 == t3;
-  const uint32_t e12 = t1 == t2, e13 = t1 == t3, e23 = t2 == t3;
-  // first appearances of a state among the neighbours
-  const bool f1 = !e01, f2 = !(e02 | e12), f3 = !(e03 | e13 | e23);
-  const uint32_t w0 = sW[1 + e01 + e02 + e03];
-  const uint32_t w1 = sW[f1 ? 1 + e12 + e13 : 5];
-  const uint32_t w2 = sW[f2 ? 1 + e23 : 5];
-  const uint32_t w3 = sW[f3 ? 1 : 5];
-  const uint32_t k = 1u + f1 + f2 + f3;  // distinct neighbour states
-  const uint32_t s1 = w0, s2 = s1 + w1, s3 = s2 + w2, s4 = s3 + w3;
-  const uint32_t Z = s4 + (q - k) * sW[0];
-  const uint32_t r = __umulhi(u, Z);
-  // states no neighbour holds: the idx-th of them in increasing order is idx
-  // moved past every held state at or below it (held states sorted; a
-  // repeated neighbour is replaced by 256, above every state)
-  uint32_t d0 = t0, d1 = f1 ? t1 : 256u, d2 = f2 ? t2 : 256u,
-           d3 = f3 ? t3 : 256u;
-  hb_cswap(d0, d1);
-  hb_cswap(d2, d3);
-  hb_cswap(d0, d2);
-  hb_cswap(d1, d3);
-  hb_cswap(d1, d2);
-  uint32_t s = (r - s4) >> m;
-  s += d0 <= s;
-  s += d1 <= s;
-  s += d2 <= s;
-  s += d3 <= s;
-  s = r < s4 ? t3 : s;
-  s = r < s3 ? t2 : s;
-  s = r < s2 ? t1 : s;
-  s = r < s1 ? t0 : s;
+  const uint32_t code = (uint32_t)(t0 == t1) | (uint32_t)(t0 == t2) << 1 |
+                        (uint32_t)(t0 == t3) << 2 | (uint32_t)(t1 == t2) << 3 |
+                        (uint32_t)(t1 == t3) << 4 | (uint32_t)(t2 == t3) << 5;
+  const uint32_t *e = sW + 8 + 8 * code;
+  const uint4 sb = *reinterpret_cast<const uint4 *>(e);
+  const uint32_t r = __umulhi(u, e[4]);
+  uint32_t s = (r - sb.w) >> m;
+  s = r < sb.w ? t3 : s;
+  s = r < sb.z ? t2 : s;
+  s = r < sb.y ? t1 : s;
+  s = r < sb.x ? t0 : s;
   // s < q already; the clamp keeps the shared histogram in bounds whatever
   // the spins in memory hold
   return min(s, q - 1u);
@@ -121,18 +99,6 @@ __device__ __forceinline__ uint32_t hb_site(uint32_t t0, uint32_t t1,
 
 __device__ __forceinline__ uint32_t hb_byte(uint32_t w, int b) {
   return __byte_perm(w, 0u, 0x4440u + (uint32_t)b);
-}
-
-// 1 per byte where a >= b, for bytes below 128.
-__device__ __forceinline__ uint32_t hb_ge(uint32_t a, uint32_t b) {
-  return (((a | 0x80808080u) - b) & 0x80808080u) >> 7;
-}
-
-// The same with a | 0x80808080 given and the subtraction issued as a
-// multiply-add (b * neg + aM, neg = -1 at run time) on the FMA-heavy pipe.
-__device__ __forceinline__ uint32_t hb_ge_m(uint32_t aM, uint32_t b,
-                                            uint32_t neg) {
-  return ((b * neg + aM) & 0x80808080u) >> 7;
 }
 
 // Bit FROM of every byte moved to bit TO and added to acc (the fields are
@@ -148,19 +114,16 @@ __device__ __forceinline__ uint32_t hb_put(uint32_t x, uint32_t acc,
 }
 
 // The four sites of one word at once (spins < 2^QB, QB <= 6): the same
-// rule as hb_site, with the neighbour comparisons and first appearances
-// done per byte on whole words, the interval bounds and normaliser read
-// from the pattern table, and the unheld-state index moved past the held
-// states by their ranks instead of a sort (the idx-th unheld state is
-// idx + #{held d : d - rank(d) <= idx}).
+// rule as hb_site, with the six neighbour equalities done per byte on whole
+// words and packed into the four sites' pattern codes, the interval bounds
+// and normaliser read from the pattern table per site, and the new byte
+// merged in from the neighbour word of the interval r falls in.
 // U, D, Lw, Rw: neighbour words (up, down, left, right); uw: Philox words;
 // sW: the launch's table (hb_build_table).
-// one: the run-time 1 of PassArgs.  The rule is mostly byte-SIMD ALU work,
-// so its additions, subtractions (x * neg + y with neg = -1 at run time) and
-// bit-field moves issue as multiply-adds on the FMA-heavy pipe, which this
-// pass otherwise leaves two thirds idle; every step is exact 32-bit
-// arithmetic whose per-byte results stay in 0..255, so the order of the
-// additions does not matter.
+// one: the run-time 1 of PassArgs.  The equality tests' additions and the
+// code's bit-field moves issue as multiply-adds on the FMA-heavy pipe,
+// which this pass otherwise leaves largely idle; every step is exact 32-bit
+// arithmetic.
 template <int QB>
 __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
                                             uint32_t Lw, uint32_t Rw,
@@ -169,9 +132,6 @@ __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
                                             uint32_t one) {
   static_assert(QB <= 6, "byte sums below need spins < 64");
   constexpr uint32_t K = Swar<QB>::K, M = Swar<QB>::M;
-  constexpr uint32_t ONE = 0x01010101u, HI = 0x80808080u;
-  constexpr uint32_t SENT = 0x7F7F7F7Fu;  // above every state < 64
-  const uint32_t neg = 0u - one;          // -1 at run time
   // 2^QB per byte where two neighbours are equal
   const uint32_t E01 = ~((U ^ D) * one + K) & M;
   const uint32_t E02 = ~((U ^ Lw) * one + K) & M;
@@ -186,58 +146,28 @@ __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
   CODE = hb_put<QB, 3>(E12, CODE, one);
   CODE = hb_put<QB, 4>(E13, CODE, one);
   CODE = hb_put<QB, 5>(E23, CODE, one);
-  // first appearances (1 per byte) and their byte masks
-  const uint32_t F1 = (E01 ^ M) >> QB;
-  const uint32_t F2 = (~(E02 | E12) & M) >> QB;
-  const uint32_t F3 = (~(E03 | E13 | E23) & M) >> QB;
-  const uint32_t m1 = F1 * 0xFFu, m2 = F2 * 0xFFu, m3 = F3 * 0xFFu;
-  // held states (repeats replaced by SENT), their ranks and thresholds
-  const uint32_t H1 = (D & m1) | (SENT & ~m1);
-  const uint32_t H2 = (Lw & m2) | (SENT & ~m2);
-  const uint32_t H3 = (Rw & m3) | (SENT & ~m3);
-  const uint32_t UM = U | HI, H1M = H1 | HI, H2M = H2 | HI;
-  const uint32_t g01 = hb_ge_m(UM, H1, neg), g02 = hb_ge_m(UM, H2, neg),
-                 g03 = hb_ge_m(UM, H3, neg);
-  const uint32_t g12 = hb_ge_m(H1M, H2, neg), g13 = hb_ge_m(H1M, H3, neg),
-                 g23 = hb_ge_m(H2M, H3, neg);
-  // T_i = held state i minus its rank among the held states
-  const uint32_t T0 = g03 * neg + (g02 * neg + (g01 * neg + U));
-  const uint32_t T1 =
-      g13 * neg + (g12 * neg + (g01 * one + (H1 * one + (0u - ONE))));
-  const uint32_t T2 =
-      g23 * neg + (g12 * one + (g02 * one + (H2 * one + (0u - 2u * ONE))));
-  const uint32_t T3 =
-      g23 * one + (g13 * one + (g03 * one + (H3 * one + (0u - 3u * ONE))));
   const uint8_t *ent = reinterpret_cast<const uint8_t *>(sW + 8);
-  uint32_t idx[4], cls[4];
+  uint32_t idx[4], r[4];
+  uint4 sb[4];
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     const uint32_t off = hb_byte(CODE, b) * 32u;
-    const uint4 sb = *reinterpret_cast<const uint4 *>(ent + off);
+    sb[b] = *reinterpret_cast<const uint4 *>(ent + off);
     const uint32_t Z = *reinterpret_cast<const uint32_t *>(ent + off + 16);
-    const uint32_t r = __umulhi(uw[b], Z);
-    idx[b] = min((sb.w * neg + r) >> m, 0x40u);  // < q - k <= 62 when used
-    cls[b] = (uint32_t)(r >= sb.x) + (uint32_t)(r >= sb.y) +
-             (uint32_t)(r >= sb.z) + (uint32_t)(r >= sb.w);
+    r[b] = __umulhi(uw[b], Z);
+    // the state among the bases; its low byte is replaced below whenever
+    // r < s4, so only r >= s4 (idx < q) reaches the result
+    idx[b] = (r[b] - sb[b].w) >> m;
   }
-  const uint32_t IDX = pack4(idx[0], idx[1], idx[2], idx[3]);
-  const uint32_t CLS = pack4(cls[0], cls[1], cls[2], cls[3]);
-  const uint32_t IDXM = IDX | HI;
-  const uint32_t P =
-      hb_ge_m(IDXM, T3, neg) * one +
-      (hb_ge_m(IDXM, T2, neg) * one +
-       (hb_ge_m(IDXM, T1, neg) * one + (hb_ge_m(IDXM, T0, neg) * one + IDX)));
-  // per byte: class 0..3 takes that neighbour, 4 the unheld state; ne(c) is
-  // 0xFF where the class differs from c
-  auto ne = [&](uint32_t c) {
-    const uint32_t x = CLS ^ (c * ONE);  // 0 where equal, bytes < 8
-    return ((((x * one + 0x7F7F7F7Fu) | x) & HI) >> 7) * 0xFFu;
-  };
-  uint32_t N = P;
-  N = (N & ne(0u)) | (U & ~ne(0u));
-  N = (N & ne(1u)) | (D & ~ne(1u));
-  N = (N & ne(2u)) | (Lw & ~ne(2u));
-  N = (N & ne(3u)) | (Rw & ~ne(3u));
+  uint32_t N = pack4(idx[0], idx[1], idx[2], idx[3]);
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const uint32_t Mb = 0xFFu << (8 * b);
+    if (r[b] < sb[b].w) N = (N & ~Mb) | (Rw & Mb);
+    if (r[b] < sb[b].z) N = (N & ~Mb) | (Lw & Mb);
+    if (r[b] < sb[b].y) N = (N & ~Mb) | (D & Mb);
+    if (r[b] < sb[b].x) N = (N & ~Mb) | (U & Mb);
+  }
   return N;
 }
 

@@ -55,9 +55,12 @@ MUTATIONS = {
         "      double x = ldexp(exp(beta * (double)n), m);",
         "      double x = ldexp(exp(0.5 * beta * (double)n), m);",
         "hb_distribution"),
-    "hb_unheld_states_include_held": (
-        "      for (int a = 0; a < 4; ++a) held |= nb[a] == x;",
-        "      for (int a = 0; a < 4; ++a) held |= 0;", "hb_distribution"),
+    "hb_excess_includes_base": (
+        "    const uint64_t excess = W[cnt[b]] - W[0];",
+        "    const uint64_t excess = W[cnt[b]];", "hb_distribution"),
+    "hb_normaliser_misses_held_bases": (
+        "  uint64_t Z = (uint64_t)q * W[0];",
+        "  uint64_t Z = (uint64_t)(q - k) * W[0];", "hb_distribution"),
     "hb_dB_sign": ("  *dB = n_now - n_old;", "  *dB = n_old - n_now;",
                    "hb_recount"),
 }

@@ -105,18 +105,19 @@ def test_metropolis_decision_index_and_counts(QB):
 # -------------------------------------------------------------- heat bath
 
 def _pattern_table(W, q, m):
-    """hb_pattern_entry for the 64 codes: rows (s1, s2, s3, s4, Z)."""
-    sW = [int(x) for x in W] + [0, 0, 0]
+    """hb_pattern_entry for the 64 codes: rows (s1, s2, s3, s4, Z), the
+    cumulative excesses W[c] - W[0] of the neighbours' classes (a repeated
+    neighbour adds none) and Z = s4 + q 2^m."""
+    ex = [0] + [int(W[c]) - int(W[0]) for c in range(1, 5)] + [0]
     t = np.zeros((64, 5), dtype=np.uint64)
     for code in range(64):
         e01, e02, e03, e12, e13, e23 = ((code >> i) & 1 for i in range(6))
         f1, f2, f3 = e01 ^ 1, (e02 | e12) ^ 1, (e03 | e13 | e23) ^ 1
         c = [1 + e01 + e02 + e03, 1 + e12 + e13 if f1 else 5,
              1 + e23 if f2 else 5, 1 if f3 else 5]
-        s = np.cumsum([sW[x] for x in c]) & M32
-        k = 1 + f1 + f2 + f3
+        s = np.cumsum([ex[x] for x in c]) & M32
         t[code, :4] = s
-        t[code, 4] = (int(s[3]) + (((q - k) << m) & M32)) & M32
+        t[code, 4] = (int(s[3]) + ((q << m) & M32)) & M32
     return t
 
 
@@ -126,7 +127,6 @@ def _hb_word(QB, U, D, Lw, Rw, uw, tab, m):
     u = np.uint64
     K = u(0x01010101 * ((1 << QB) - 1))
     M = u(0x01010101 * (1 << QB))
-    ONE, SENT, HI = u(0x01010101), u(0x7F7F7F7F), u(0x80808080)
 
     def eq(a, b):
         return ((((a ^ b) + K) & u(M32)) ^ u(M32)) & M
@@ -134,46 +134,20 @@ def _hb_word(QB, U, D, Lw, Rw, uw, tab, m):
     def mv(x, to):
         return x >> u(QB - to) if QB >= to else (x << u(to - QB)) & u(M32)
 
-    def ge(a, b):
-        return (((a | HI) - b) & HI) >> u(7)
-
-    def sel(a, b, msk):
-        return (a & msk) | (b & (msk ^ u(M32)))
-
     E01, E02, E03 = eq(U, D), eq(U, Lw), eq(U, Rw)
     E12, E13, E23 = eq(D, Lw), eq(D, Rw), eq(Lw, Rw)
     CODE = mv(E01, 0) | mv(E02, 1) | mv(E03, 2) | mv(E12, 3) | mv(E13, 4) | \
         mv(E23, 5)
-    F1 = (E01 ^ M) >> u(QB)
-    F2 = (((E02 | E12) ^ u(M32)) & M) >> u(QB)
-    F3 = (((E03 | E13 | E23) ^ u(M32)) & M) >> u(QB)
-    m1, m2, m3 = (F * u(0xFF) for F in (F1, F2, F3))
-    H1, H2, H3 = sel(D, SENT, m1), sel(Lw, SENT, m2), sel(Rw, SENT, m3)
-    g01, g02, g03 = ge(U, H1), ge(U, H2), ge(U, H3)
-    g12, g13, g23 = ge(H1, H2), ge(H1, H3), ge(H2, H3)
-    T = [(U - (g01 + g02 + g03)) & u(M32),
-         (H1 - ((g01 ^ ONE) + g12 + g13)) & u(M32),
-         (H2 - ((g02 ^ ONE) + (g12 ^ ONE) + g23)) & u(M32),
-         (H3 - ((g03 ^ ONE) + (g13 ^ ONE) + (g23 ^ ONE))) & u(M32)]
-    idx = np.zeros((U.size, 4), dtype=np.uint64)
-    cls = np.zeros((U.size, 4), dtype=np.uint64)
+    N = np.zeros((U.size, 4), dtype=np.uint64)
     for b in range(4):
         e = tab[_byte(CODE, b).astype(np.int64)]
         r = (uw[:, b].astype(np.uint64) * e[:, 4]) >> u(32)
-        idx[:, b] = np.minimum(((r - e[:, 3]) & u(M32)) >> u(m), u(0x40))
-        cls[:, b] = sum((r >= e[:, i]).astype(np.uint64) for i in range(4))
-    IDX, CLS = _words(idx), _words(cls)
-    P = IDX + ge(IDX, T[0]) + ge(IDX, T[1]) + ge(IDX, T[2]) + ge(IDX, T[3])
-
-    def is_(c):
-        x = CLS ^ (u(c) * ONE)
-        return ((((x + u(0x7F7F7F7F)) | x) & HI) >> u(7)) * u(0xFF) ^ u(M32)
-
-    N = P
-    for c, src in enumerate((U, D, Lw, Rw)):
-        msk = is_(c)
-        N = (src & msk) | (N & (msk ^ u(M32)))
-    return N
+        n = (((r - e[:, 3]) & u(M32)) >> u(m)) & u(0xFF)
+        # later (lower) bounds overwrite: the first interval holding r wins
+        for i, src in ((3, Rw), (2, Lw), (1, D), (0, U)):
+            n = np.where(r < e[:, i], _byte(src, b), n)
+        N[:, b] = n
+    return _words(N)
 
 
 @pytest.mark.parametrize("q,beta,nv", [(3, 0.8, 3), (9, np.log(4.0), 9),
