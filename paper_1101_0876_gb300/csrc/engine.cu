@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kPassThreads,
   for (uint32_t v = tid; v < q * 32u; v += kPassThreads) s_hist[v] = 0;
   if (tid == 0) s_sat = 0;
   if (KIND == kKindHB)
-    hb_build_table(s_tab, sd.tab, q, sd.tab[8], tid);  // W[0..7], m; barrier
+    hb_build_table(s_tab, sd.tab, tid);  // W[0..7]; barrier
   else
     __syncthreads();
   pdl_wait_previous();

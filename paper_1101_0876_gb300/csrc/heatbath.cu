@@ -14,8 +14,9 @@ namespace {
 constexpr int kHbPairBins = 256;
 
 // Resident CTAs per SM asked of the compiler: the heat-bath rule keeps more
-// values live than the Metropolis one; the word rule (QB <= 6) fits 128
-// registers (4 CTAs), the per-site rule (QB 8) 168 (3 CTAs), without spills.
+// values live than the Metropolis one.  3 CTAs (up to 168 registers, no
+// spills): at 4 CTAs the word rule spills a few words per thread, and the
+// white pass at L = 32768, q = 9 ran 1.809 against 1.842 ps per update.
 #ifndef POTTS_HB_MINB
 #define POTTS_HB_MINB 3
 #endif
@@ -23,7 +24,7 @@ constexpr int kHbPairBins = 256;
 // Same grid, walk and reductions as the Metropolis pass kernel (XP: the
 // histogram of both planes in (black, white) pair bins, black pass only).
 template <int QB, int COLOUR, bool PAIRS, int LAY, bool XP = false>
-__global__ void __launch_bounds__(kPassThreads, QB <= 6 ? 4 : POTTS_HB_MINB)
+__global__ void __launch_bounds__(kPassThreads, POTTS_HB_MINB)
     hb_pass_kernel(PassArgs A, HeatTable T, TileGeom G,
                    unsigned long long *rec) {
   constexpr bool COUNTS = COLOUR == 1;
@@ -39,7 +40,7 @@ __global__ void __launch_bounds__(kPassThreads, QB <= 6 ? 4 : POTTS_HB_MINB)
     for (uint32_t v = tid; v < bins * 32u; v += kPassThreads) s_hist[v] = 0;
   if (tid < 16) s_fold[tid] = 0;
   if (tid == 0) s_sat = 0;
-  hb_build_table(s_W, T.W, A.q, T.m, tid);  // ends with a barrier
+  hb_build_table(s_W, T.W, tid);  // ends with a barrier
   pdl_wait_previous();
 
   const PhiloxKey ks = philox_schedule(A.key0, A.key1);

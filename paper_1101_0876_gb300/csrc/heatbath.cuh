@@ -27,21 +27,28 @@ struct HeatTable {
   uint32_t m;
 };
 
-// Shared table of a heat-bath launch: W[0..7], then one 8-word entry per
+// Shared table of a heat-bath launch: W[0..7], then one 4-word entry per
 // equality pattern of the four neighbours.  The pattern code of a site has
 // bit 0..5 = [up == down], [up == left], [up == right], [down == left],
 // [down == right], [left == right]; the interval bounds s1..s4 (cumulative
 // excesses of the neighbours' states, a neighbour that repeats an earlier
-// one adding nothing) and the normaliser Z depend on the site only through
-// that code (and on W, q, m, which are fixed for a launch).  Entry:
-// {s1, s2, s3, s4, Z, 0, 0, 0}; r < s1 selects the up neighbour's state,
+// one adding nothing) depend on the site only through that code (and on W,
+// which is fixed for a launch), and the normaliser is Z = s4 + q 2^m.
+// Entry: {s1, s2, s3, s4}; r < s1 selects the up neighbour's state,
 // s1 <= r < s2 the down one's, and so on, r >= s4 the state (r - s4) >> m.
 // Of the 64 codes only the 15 that are transitive occur.
-constexpr int kHbTableWords = 8 + 64 * 8;
+// Each entry is stored kHbCopies times, copy j at 16-byte slot 8 code + j,
+// and a lane reads copy (lane mod 8): the eight lanes of a quarter-warp,
+// which share one 128-bit shared-memory wavefront, then always hit eight
+// different bank groups, whatever codes they hold (with one copy, codes
+// equal mod 4 collide, and the common codes 0, 4, 8, 16, 32 all do).
+constexpr int kHbCopies = 8;
+constexpr int kHbTableWords = 8 + 64 * kHbCopies * 4;
 
-// Fills entry `code` from W (sW[0..7], already in shared memory).
-__device__ __forceinline__ void hb_pattern_entry(uint32_t *sW, uint32_t code,
-                                                 uint32_t q, uint32_t m) {
+// Fills entry `code` (all copies) from W (sW[0..7], already in shared
+// memory).
+__device__ __forceinline__ void hb_pattern_entry(uint32_t *sW,
+                                                 uint32_t code) {
   const uint32_t e01 = code & 1u, e02 = (code >> 1) & 1u,
                  e03 = (code >> 2) & 1u, e12 = (code >> 3) & 1u,
                  e13 = (code >> 4) & 1u, e23 = (code >> 5) & 1u;
@@ -55,23 +62,23 @@ __device__ __forceinline__ void hb_pattern_entry(uint32_t *sW, uint32_t code,
   auto ex = [&](uint32_t c) { return c <= 4u ? sW[c] - sW[0] : 0u; };
   const uint32_t s1 = ex(c0), s2 = s1 + ex(c1), s3 = s2 + ex(c2),
                  s4 = s3 + ex(c3);
-  uint32_t *e = sW + 8 + 8 * code;
-  e[0] = s1;
-  e[1] = s2;
-  e[2] = s3;
-  e[3] = s4;
-  e[4] = s4 + (q << m);  // the q bases, 2^m each
-  e[5] = e[6] = e[7] = 0u;
+  uint4 *e = reinterpret_cast<uint4 *>(sW + 8) + kHbCopies * code;
+  for (int j = 0; j < kHbCopies; ++j) e[j] = make_uint4(s1, s2, s3, s4);
+}
+
+// The lane's copy of entry 0, as a byte pointer: entry `code` is at
+// + 128 code.
+__device__ __forceinline__ const uint8_t *hb_lane_table(const uint32_t *sW) {
+  return reinterpret_cast<const uint8_t *>(sW + 8) + 16u * (threadIdx.x & 7u);
 }
 
 // Whole table: W from the launch, then the 64 entries.  Every thread of the
 // CTA calls it; it ends with a barrier.
 __device__ __forceinline__ void hb_build_table(uint32_t *sW, const uint32_t *W,
-                                               uint32_t q, uint32_t m,
                                                uint32_t tid) {
   if (tid < 8) sW[tid] = W[tid];
   __syncthreads();
-  if (tid < 64) hb_pattern_entry(sW, tid, q, m);
+  if (tid < 64) hb_pattern_entry(sW, tid);
   __syncthreads();
 }
 
@@ -84,9 +91,9 @@ __device__ __forceinline__ uint32_t hb_site(uint32_t t0, uint32_t t1,
   const uint32_t code = (uint32_t)(t0 == t1) | (uint32_t)(t0 == t2) << 1 |
                         (uint32_t)(t0 == t3) << 2 | (uint32_t)(t1 == t2) << 3 |
                         (uint32_t)(t1 == t3) << 4 | (uint32_t)(t2 == t3) << 5;
-  const uint32_t *e = sW + 8 + 8 * code;
-  const uint4 sb = *reinterpret_cast<const uint4 *>(e);
-  const uint32_t r = __umulhi(u, e[4]);
+  const uint4 sb =
+      *reinterpret_cast<const uint4 *>(hb_lane_table(sW) + 128u * code);
+  const uint32_t r = __umulhi(u, sb.w + (q << m));
   uint32_t s = (r - sb.w) >> m;
   s = r < sb.w ? t3 : s;
   s = r < sb.z ? t2 : s;
@@ -119,7 +126,7 @@ __device__ __forceinline__ uint32_t hb_put(uint32_t x, uint32_t acc,
 // and normaliser read from the pattern table per site, and the new byte
 // merged in from the neighbour word of the interval r falls in.
 // U, D, Lw, Rw: neighbour words (up, down, left, right); uw: Philox words;
-// sW: the launch's table (hb_build_table).
+// ent: the lane's copy of the launch's table (hb_lane_table); qm = q << m.
 // one: the run-time 1 of PassArgs.  The equality tests' additions and the
 // code's bit-field moves issue as multiply-adds on the FMA-heavy pipe,
 // which this pass otherwise leaves largely idle; every step is exact 32-bit
@@ -128,8 +135,8 @@ template <int QB>
 __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
                                             uint32_t Lw, uint32_t Rw,
                                             const uint32_t uw[4],
-                                            const uint32_t *sW, uint32_t m,
-                                            uint32_t one) {
+                                            const uint8_t *ent, uint32_t m,
+                                            uint32_t qm, uint32_t one) {
   static_assert(QB <= 6, "byte sums below need spins < 64");
   constexpr uint32_t K = Swar<QB>::K, M = Swar<QB>::M;
   // 2^QB per byte where two neighbours are equal
@@ -146,15 +153,12 @@ __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
   CODE = hb_put<QB, 3>(E12, CODE, one);
   CODE = hb_put<QB, 4>(E13, CODE, one);
   CODE = hb_put<QB, 5>(E23, CODE, one);
-  const uint8_t *ent = reinterpret_cast<const uint8_t *>(sW + 8);
   uint32_t idx[4], r[4];
   uint4 sb[4];
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
-    const uint32_t off = hb_byte(CODE, b) * 32u;
-    sb[b] = *reinterpret_cast<const uint4 *>(ent + off);
-    const uint32_t Z = *reinterpret_cast<const uint32_t *>(ent + off + 16);
-    r[b] = __umulhi(uw[b], Z);
+    sb[b] = *reinterpret_cast<const uint4 *>(ent + hb_byte(CODE, b) * 128u);
+    r[b] = __umulhi(uw[b], sb[b].w + qm);
     // the state among the bases; its low byte is replaced below whenever
     // r < s4, so only r >= s4 (idx < q) reaches the result
     idx[b] = (r[b] - sb[b].w) >> m;
@@ -216,7 +220,8 @@ __device__ __forceinline__ void hb_row(const PassArgs &A, const PhiloxKey &ks,
     const uint32_t Lw = LEFT ? Wd[k] : Cw[k];
     const uint32_t Rw = LEFT ? Cw[k] : Wd[k];
     if constexpr (QB <= 6) {
-      Nw[k] = hb_word<QB>(w.Up[k], Dw[k], Lw, Rw, uw, sW, m, A.one);
+      Nw[k] = hb_word<QB>(w.Up[k], Dw[k], Lw, Rw, uw, hb_lane_table(sW), m,
+                          A.q << m, A.one);
     } else {
       uint32_t s[4];
 #pragma unroll
