@@ -167,9 +167,7 @@ __global__ void __launch_bounds__(kPassThreads,
   __syncthreads();
   if (COUNTS && tid == 0 && s_sat) atomicAdd(rec, (unsigned long long)s_sat);
   for (uint32_t v = tid; v < q; v += kPassThreads) {
-    uint32_t sum = 0;
-#pragma unroll 8
-    for (int l = 0; l < 32; ++l) sum += s_hist[v * 32u + l];
+    const uint32_t sum = bin_sum(s_hist, v);
     if (sum) atomicAdd(rec + 1 + v, (unsigned long long)sum);
   }
 }

@@ -69,9 +69,7 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_HB_MINB)
   if (!HIST) return;
   if (PBINS) {
     for (uint32_t p = tid; p < (uint32_t)kHbPairBins; p += kPassThreads) {
-      uint32_t sum = 0;
-#pragma unroll 8
-      for (int l = 0; l < 32; ++l) sum += s_hist[p * 32u + l];
+      const uint32_t sum = bin_sum(s_hist, p);
       if (sum) {
         atomicAdd(&s_fold[p & 15u], sum);
         atomicAdd(&s_fold[p >> 4], sum);
@@ -82,9 +80,7 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_HB_MINB)
       atomicAdd(rec + 1 + tid, (unsigned long long)s_fold[tid]);
   } else {
     for (uint32_t v = tid; v < A.q; v += kPassThreads) {
-      uint32_t sum = 0;
-#pragma unroll 8
-      for (int l = 0; l < 32; ++l) sum += s_hist[v * 32u + l];
+      const uint32_t sum = bin_sum(s_hist, v);
       if (sum) atomicAdd(rec + 1 + v, (unsigned long long)sum);
     }
   }

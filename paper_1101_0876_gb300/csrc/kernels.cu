@@ -79,9 +79,7 @@ __global__ void __launch_bounds__(kPassThreads,
   if (PBINS) {
     // fold pair bins (v0 | v1 << 4) back to the 16 states
     for (uint32_t p = tid; p < (uint32_t)kPairBins; p += kPassThreads) {
-      uint32_t sum = 0;
-#pragma unroll 8
-      for (int l = 0; l < 32; ++l) sum += s_hist[p * 32u + l];
+      const uint32_t sum = bin_sum(s_hist, p);
       if (sum) {
         atomicAdd(&s_fold[p & 15u], sum);
         atomicAdd(&s_fold[p >> 4], sum);
@@ -92,9 +90,7 @@ __global__ void __launch_bounds__(kPassThreads,
       atomicAdd(rec + 1 + tid, (unsigned long long)s_fold[tid]);
   } else {
     for (uint32_t v = tid; v < A.q; v += kPassThreads) {
-      uint32_t sum = 0;
-#pragma unroll 8
-      for (int l = 0; l < 32; ++l) sum += s_hist[v * 32u + l];
+      const uint32_t sum = bin_sum(s_hist, v);
       if (sum) atomicAdd(rec + 1 + v, (unsigned long long)sum);
     }
   }
@@ -146,9 +142,7 @@ __global__ void __launch_bounds__(kPassThreads, kMinbNib)
   __syncthreads();
   if (COUNTS && tid == 0 && s_sat) atomicAdd(rec, (unsigned long long)s_sat);
   for (uint32_t p = tid; p < (uint32_t)kPairBins; p += kPassThreads) {
-    uint32_t sum = 0;
-#pragma unroll 8
-    for (int l = 0; l < 32; ++l) sum += s_hist[p * 32u + l];
+    const uint32_t sum = bin_sum(s_hist, p);
     if (sum) {
       atomicAdd(&s_fold[p & 15u], sum);
       atomicAdd(&s_fold[p >> 4], sum);
@@ -426,8 +420,7 @@ __global__ void recount_kernel(const uint8_t *white, const uint8_t *black,
   __syncthreads();
   if (tid == 0 && s_sat) atomicAdd(rec, (unsigned long long)s_sat);
   for (uint32_t v = tid; v < q; v += blockDim.x) {
-    uint32_t sum = 0;
-    for (int l = 0; l < 32; ++l) sum += s_hist[v * 32u + l];
+    const uint32_t sum = bin_sum(s_hist, v);
     if (sum) atomicAdd(rec + 1 + v, (unsigned long long)sum);
   }
 }

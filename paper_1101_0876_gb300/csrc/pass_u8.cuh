@@ -207,6 +207,18 @@ __device__ __forceinline__ void hist_word(uint32_t *lane_hist, uint32_t w) {
   }
 }
 
+// Count of bin v summed over the 32 lanes' counters (lane l's counter of
+// bin v at v * 32 + l).  Lane l starts at counter (l + v) mod 32, so when the
+// threads of a warp fold consecutive bins each step's 32 loads hit 32
+// different banks (in lane order they would all hit bank l).
+__device__ __forceinline__ uint32_t bin_sum(const uint32_t *s_hist,
+                                            uint32_t v) {
+  uint32_t sum = 0;
+#pragma unroll 8
+  for (uint32_t l = 0; l < 32u; ++l) sum += s_hist[v * 32u + ((l + v) & 31u)];
+  return sum;
+}
+
 // Histogram of one black word's new spins paired with the white spins at
 // the same plane position (q <= 16): byte b of nw + (cw << 4) is the bin
 // (black spin, white spin), so four shared atomics count eight sites and
