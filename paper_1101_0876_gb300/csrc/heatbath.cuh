@@ -241,7 +241,7 @@ __device__ __forceinline__ void hb_row(const PassArgs &A, const PhiloxKey &ks,
   if constexpr (XP) {
     if (COUNTS) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) hist_cross(lane_hist, Nw[k], Cw[k]);
+      for (int k = 0; k < 4; ++k) hist_cross(lane_hist, Nw[k], Cw[k], 1u);
     }
   } else {
 #pragma unroll

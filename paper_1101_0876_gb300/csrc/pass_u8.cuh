@@ -225,10 +225,12 @@ __device__ __forceinline__ uint32_t bin_sum(const uint32_t *s_hist,
 // the white pass keeps no histogram.  The white plane is final when the
 // black pass runs, and the black walks read every white word of their rows
 // exactly once as the centre row.  Bytes above 15 (planes the caller did
-// not check) can only scramble the bins, never leave them.
+// not check) can only scramble the bins, never leave them.  one: 1, as a
+// literal (the pair forms on the ALU pipe) or the run-time 1 of PassArgs
+// (a multiply-add on the FMA-heavy pipe).
 __device__ __forceinline__ void hist_cross(uint32_t *lane_hist, uint32_t nw,
-                                           uint32_t cw) {
-  const uint32_t t = nw + (cw << 4);
+                                           uint32_t cw, uint32_t one) {
+  const uint32_t t = cw * (one << 4) + nw;
 #pragma unroll
   for (int b = 0; b < 4; ++b)
     atomicAdd(lane_hist + __byte_perm(t, 0u, 0x4440u + (uint32_t)b) * 32u, 1u);
@@ -382,10 +384,12 @@ __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
     uint32_t no16 = 0, nn16 = 0;
     // the white pass moves its additions to the FMA-heavy pipe; the black
     // pass, whose counts already add multiply-adds, keeps them on the ALU
-    // (1.2930 against 1.2893 ps per update at L = 32768)
+    // (1.2930 against 1.2893 ps per update at L = 32768 with a histogram per
+    // pass), except with the cross-plane histogram (XP), whose extra ALU
+    // work tips it the other way (1.1993 against 1.2062 ps)
     const uint32_t idx =
         delta_index<QB, COUNTS>(w.S[k], P, w.Up[k], Dw[k], Cw[k], Wd[k], &no16,
-                                &nn16, COUNTS ? 1u : A.one);
+                                &nn16, (COUNTS && !XP) ? 1u : A.one);
     const uint32_t m = accept_mask<LT0>(idx, (uint32_t)r0, (uint32_t)r1,
                                         (uint32_t)r2, (uint32_t)r3, tab);
     Nw[k] = (P & m) | (w.S[k] & ~m);
@@ -399,7 +403,7 @@ __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
   if constexpr (XP) {
     if (COUNTS) {
 #pragma unroll
-      for (int k = 0; k < NW; ++k) hist_cross(lane_hist, Nw[k], Cw[k]);
+      for (int k = 0; k < NW; ++k) hist_cross(lane_hist, Nw[k], Cw[k], 1u);
     }
   } else {
 #pragma unroll
