@@ -15,8 +15,8 @@ constexpr int kHbPairBins = 256;
 
 // Resident CTAs per SM asked of the compiler: the heat-bath rule keeps more
 // values live than the Metropolis one.  3 CTAs (up to 168 registers, no
-// spills): at 4 CTAs the word rule spills a few words per thread, and the
-// white pass at L = 32768, q = 9 ran 1.809 against 1.842 ps per update.
+// spills); 4 CTAs fit the word rule without spills too and measured the
+// same (1.585 against 1.587 ps per update at L = 32768, q = 9).
 #ifndef POTTS_HB_MINB
 #define POTTS_HB_MINB 3
 #endif

@@ -124,7 +124,8 @@ __device__ __forceinline__ uint32_t hb_put(uint32_t x, uint32_t acc,
 // rule as hb_site, with the six neighbour equalities done per byte on whole
 // words and packed into the four sites' pattern codes, the interval bounds
 // and normaliser read from the pattern table per site, and the new byte
-// merged in from the neighbour word of the interval r falls in.
+// taken from a whole-word select among the four neighbour words and the
+// base state (four compares and selects a site, then one masked OR).
 // U, D, Lw, Rw: neighbour words (up, down, left, right); uw: Philox words;
 // ent: the lane's copy of the launch's table (hb_lane_table); qm = q << m.
 // one: the run-time 1 of PassArgs.  The equality tests' additions and the
@@ -153,24 +154,22 @@ __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
   CODE = hb_put<QB, 3>(E12, CODE, one);
   CODE = hb_put<QB, 4>(E13, CODE, one);
   CODE = hb_put<QB, 5>(E23, CODE, one);
-  uint32_t idx[4], r[4];
-  uint4 sb[4];
+  const uint32_t neg = 0u - one;  // -1 at run time
+  uint32_t N = 0;
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
-    sb[b] = *reinterpret_cast<const uint4 *>(ent + hb_byte(CODE, b) * 128u);
-    r[b] = __umulhi(uw[b], sb[b].w + qm);
-    // the state among the bases; its low byte is replaced below whenever
-    // r < s4, so only r >= s4 (idx < q) reaches the result
-    idx[b] = (r[b] - sb[b].w) >> m;
-  }
-  uint32_t N = pack4(idx[0], idx[1], idx[2], idx[3]);
-#pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    const uint32_t Mb = 0xFFu << (8 * b);
-    if (r[b] < sb[b].w) N = (N & ~Mb) | (Rw & Mb);
-    if (r[b] < sb[b].z) N = (N & ~Mb) | (Lw & Mb);
-    if (r[b] < sb[b].y) N = (N & ~Mb) | (D & Mb);
-    if (r[b] < sb[b].x) N = (N & ~Mb) | (U & Mb);
+    const uint4 sb =
+        *reinterpret_cast<const uint4 *>(ent + hb_byte(CODE, b) * 128u);
+    const uint32_t r = __umulhi(uw[b], sb.w * one + qm);
+    // whole-word candidates, each holding site b's answer in byte b: first
+    // the state among the bases (< q when r >= s4; when r < s4 a neighbour
+    // word below replaces it), then the neighbour of the first bound above r
+    uint32_t t = ((sb.w * neg + r) >> m) * (one << (8 * b));
+    t = r < sb.w ? Rw : t;
+    t = r < sb.z ? Lw : t;
+    t = r < sb.y ? D : t;
+    t = r < sb.x ? U : t;
+    N |= t & (0xFFu << (8 * b));
   }
   return N;
 }
