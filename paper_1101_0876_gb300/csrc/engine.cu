@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kPassThreads,
                       const StepDesc *__restrict__ S, int32_t s) {
   constexpr bool COUNTS = COLOUR == 1;
   constexpr bool LT0 = KIND == kKindLT0;
-  extern __shared__ uint32_t s_hist[];
+  extern __shared__ __align__(16) uint32_t s_hist[];
   __shared__ __align__(16) uint32_t s_tab[KIND == kKindHB ? kHbTableWords
                                                           : kTabWords];
   __shared__ uint32_t s_sat;

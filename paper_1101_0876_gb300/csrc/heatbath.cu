@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_HB_MINB)
   constexpr bool COUNTS = COLOUR == 1;
   constexpr bool HIST = !XP || COUNTS;
   constexpr bool PBINS = PAIRS || XP;
-  extern __shared__ uint32_t s_hist[];
+  extern __shared__ __align__(16) uint32_t s_hist[];
   __shared__ __align__(16) uint32_t s_W[kHbTableWords];
   __shared__ uint32_t s_sat;
   __shared__ uint32_t s_fold[16];

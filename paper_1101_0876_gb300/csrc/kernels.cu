@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kPassThreads,
   constexpr bool COUNTS = COLOUR == 1;
   constexpr bool HIST = !XP || COUNTS;     // this pass keeps a histogram
   constexpr bool PBINS = PAIRS || XP;      // 256 pair bins, folded at the end
-  extern __shared__ uint32_t s_hist[];  // bins * 32 (bins = 256 or q)
+  extern __shared__ __align__(16) uint32_t s_hist[];  // bins * 32 (bins = 256 or q)
   __shared__ __align__(16) uint32_t s_tab[kTabWords];
   __shared__ uint32_t s_sat;
   __shared__ uint32_t s_fold[16];
@@ -96,14 +96,16 @@ __global__ void __launch_bounds__(kPassThreads,
   }
 }
 
-// The U4 Metropolis pass on nibble words (pass_u4.cuh): 16 sites per thread
-// and row, pair bins (every byte of a nibble word is a pair of sites).
-template <int COLOUR, bool LT0>
-__global__ void __launch_bounds__(kPassThreads, kMinbNib)
+// The U4 Metropolis pass on nibble words (pass_u4.cuh): 8 NWN sites per
+// thread and row (16 or 32), pair bins (every byte of a nibble word is a
+// pair of sites).
+template <int COLOUR, bool LT0, int NWN>
+__global__ void __launch_bounds__(kPassThreads, NWN == 4 ? kMinb32 : kMinbNib)
     pass_u4_kernel(PassArgs A, AcceptTable Tin, TileGeom G,
                    unsigned long long *rec) {
   constexpr bool COUNTS = COLOUR == 1;
-  extern __shared__ uint32_t s_hist[];  // 256 pair bins * 32 lanes
+  constexpr int32_t SITES = 8 * NWN;
+  extern __shared__ __align__(16) uint32_t s_hist[];  // 256 pair bins * 32 lanes
   __shared__ __align__(16) uint32_t s_tab[kTabWords];
   __shared__ uint32_t s_sat;
   __shared__ uint32_t s_fold[16];
@@ -121,20 +123,20 @@ __global__ void __launch_bounds__(kPassThreads, kMinbNib)
   const int32_t cx = (int32_t)tid % G.CX, rg = (int32_t)tid / G.CX;
   const int32_t chunk = (int32_t)blockIdx.x * G.CX + cx;
   uint32_t ne = 0, rows_done = 0;
-  if (rg < G.RG && chunk * 16 < A.H) {
+  if (rg < G.RG && chunk * SITES < A.H) {
     for (int32_t tile = blockIdx.y; tile < G.ty; tile += gridDim.y) {
       const int32_t i0 = A.row_lo + (tile * G.RG + rg) * G.TR;
       if (i0 >= A.row_end) continue;
       const int32_t rows = min(G.TR, A.row_end - i0);
-      nib_walk_column<COLOUR, COUNTS, LT0>(
-          A, ks, reinterpret_cast<const uint8_t *>(s_tab), chunk * 16, i0,
+      nib_walk_column<COLOUR, COUNTS, LT0, NWN>(
+          A, ks, reinterpret_cast<const uint8_t *>(s_tab), chunk * SITES, i0,
           rows, s_hist + (tid & 31u), &ne);
       rows_done += (uint32_t)rows;
     }
   }
   pdl_release_next();
   if (COUNTS) {
-    uint32_t sat = 64u * rows_done - ne;
+    uint32_t sat = 4u * SITES * rows_done - ne;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sat += __shfl_xor_sync(0xFFFFFFFFu, sat, o);
     if ((tid & 31u) == 0 && sat) atomicAdd(&s_sat, sat);
@@ -191,20 +193,28 @@ static cudaError_t launch_qb(const PassArgs &A, const AcceptTable &T,
                   : launch_c<QB, 0, false>(A, T, G, rec, st);
 }
 
-static cudaError_t launch_u4(const PassArgs &A, const AcceptTable &T,
-                             const TileGeom &G, unsigned long long *rec,
-                             cudaStream_t st) {
+template <int NWN>
+static cudaError_t launch_u4_n(const PassArgs &A, const AcceptTable &T,
+                               const TileGeom &G, unsigned long long *rec,
+                               cudaStream_t st) {
   dim3 grid(G.gx, G.gy), block(kPassThreads);
   const size_t smem = (size_t)kPairBins * 32u * sizeof(uint32_t);
   if (T.rule_lt0)
-    return A.colour ? launch_pdl(pass_u4_kernel<1, true>, grid, block, smem,
-                                 st, A, T, G, rec)
-                    : launch_pdl(pass_u4_kernel<0, true>, grid, block, smem,
-                                 st, A, T, G, rec);
-  return A.colour ? launch_pdl(pass_u4_kernel<1, false>, grid, block, smem, st,
-                               A, T, G, rec)
-                  : launch_pdl(pass_u4_kernel<0, false>, grid, block, smem, st,
-                               A, T, G, rec);
+    return A.colour ? launch_pdl(pass_u4_kernel<1, true, NWN>, grid, block,
+                                 smem, st, A, T, G, rec)
+                    : launch_pdl(pass_u4_kernel<0, true, NWN>, grid, block,
+                                 smem, st, A, T, G, rec);
+  return A.colour ? launch_pdl(pass_u4_kernel<1, false, NWN>, grid, block,
+                               smem, st, A, T, G, rec)
+                  : launch_pdl(pass_u4_kernel<0, false, NWN>, grid, block,
+                               smem, st, A, T, G, rec);
+}
+
+static cudaError_t launch_u4(const PassArgs &A, const AcceptTable &T,
+                             const TileGeom &G, unsigned long long *rec,
+                             cudaStream_t st) {
+  if (G.sites == 32) return launch_u4_n<4>(A, T, G, rec, st);
+  return launch_u4_n<2>(A, T, G, rec, st);
 }
 
 cudaError_t launch_pass(const PassArgs &A, const AcceptTable &T,
@@ -212,7 +222,8 @@ cudaError_t launch_pass(const PassArgs &A, const AcceptTable &T,
                         cudaStream_t st) {
   if (!rec) return cudaErrorInvalidValue;
   if (A.layout == kLayoutU4) {
-    if (A.q > 16 || !G.nibble) return cudaErrorInvalidValue;
+    if (A.q > 16 || !G.nibble || (G.sites == 32 && A.H % 32))
+      return cudaErrorInvalidValue;
     return launch_u4(A, T, G, rec, st);
   }
   if (G.nibble || (G.sites == 32 && A.H % 32)) return cudaErrorInvalidValue;
@@ -294,7 +305,11 @@ TileGeom pass_geom(int32_t nrows, int32_t H, int32_t q, int32_t layout,
     return g;
   }
   if (layout == kLayoutU4) {
-    TileGeom g = choose_geom(nrows, H, q, sm_count, 0, 16, kMinbNib);
+    // 32 sites (four nibble words, one 16-byte load) per thread and row
+    // where the row allows, else 16
+    TileGeom g = (H % 32 == 0)
+                     ? choose_geom(nrows, H, q, sm_count, 0, 32, kMinb32)
+                     : choose_geom(nrows, H, q, sm_count, 0, 16, kMinbNib);
     g.pairs = 1;
     g.nibble = 1;
     return g;
@@ -370,7 +385,7 @@ __global__ void recount_kernel(const uint8_t *white, const uint8_t *black,
                                int32_t nrows, int32_t grow0, uint32_t q,
                                unsigned long long *rec) {
   using IO = Lay<LAY>;
-  extern __shared__ uint32_t s_hist[];
+  extern __shared__ __align__(16) uint32_t s_hist[];
   __shared__ uint32_t s_sat;
   const uint32_t tid = threadIdx.x;
   for (uint32_t v = tid; v < q * 32u; v += blockDim.x) s_hist[v] = 0;

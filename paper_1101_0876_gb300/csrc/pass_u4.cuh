@@ -23,9 +23,10 @@
 //     directly a pair bin;
 //   - black pass: the final unequal-neighbour count per site is X where
 //     accepted and Y where not.
-// One thread owns 16 sites (two words, 8 bytes) of a row and walks rows as
-// the byte walk does; the side neighbour word is the centre row shifted by
-// one nibble, its missing site coming from a 4-byte load (L1/L2 hit).
+// One thread owns 8 NWN sites (NWN = 2 or 4 words, 8 or 16 bytes) of a row
+// and walks rows as the byte walk does; the side neighbour word is the
+// centre row shifted by one nibble, its missing site coming from a 4-byte
+// load (L1/L2 hit).
 #pragma once
 #include <cstdint>
 
@@ -44,9 +45,10 @@ __device__ __forceinline__ uint32_t nib_ne(uint32_t a, uint32_t b,
 }
 
 // Per-thread walk state: the three other-plane rows around the current row
-// and the current own row (two nibble words each).
+// and the current own row (NWN nibble words each).
+template <int NWN>
 struct NibWalk {
-  uint32_t Up[2], Ce[2], S[2];
+  uint32_t Up[NWN], Ce[NWN], S[NWN];
   const uint8_t *oth_next;  // other plane, row i+1
   const uint8_t *oth_cur;   // other plane, row i
   uint8_t *own_cur;         // own plane, row i
@@ -54,41 +56,67 @@ struct NibWalk {
   uint32_t g0;              // Philox counter word 0 of the row's first site
 };
 
-// One row of 16 sites.  LEFT: the side neighbour is at x-1, else at x+1.
-// xb: byte offset of the window in a row; xl, xr: byte offsets of the words
-// holding the side sites; RB: bytes per plane row.
-template <bool LEFT, bool COUNTS, bool LT0>
+// NWN nibble words of a row from p (8 NWN / 2 bytes, aligned to them).
+template <int NWN, bool STREAM>
+__device__ __forceinline__ void nib_load(const uint8_t *p, uint32_t w[NWN]) {
+  if constexpr (NWN == 4) {
+    const uint4 v = STREAM ? __ldcs(reinterpret_cast<const uint4 *>(p))
+                           : __ldg(reinterpret_cast<const uint4 *>(p));
+    w[0] = v.x;
+    w[1] = v.y;
+    w[2] = v.z;
+    w[3] = v.w;
+  } else {
+    const uint2 v = STREAM ? __ldcs(reinterpret_cast<const uint2 *>(p))
+                           : __ldg(reinterpret_cast<const uint2 *>(p));
+    w[0] = v.x;
+    w[1] = v.y;
+  }
+}
+template <int NWN>
+__device__ __forceinline__ void nib_store(uint8_t *p, const uint32_t w[NWN]) {
+  if constexpr (NWN == 4)
+    __stcs(reinterpret_cast<uint4 *>(p), make_uint4(w[0], w[1], w[2], w[3]));
+  else
+    __stcs(reinterpret_cast<uint2 *>(p), make_uint2(w[0], w[1]));
+}
+
+// One row of 8 NWN sites.  LEFT: the side neighbour is at x-1, else at
+// x+1.  xb: byte offset of the window in a row; xl, xr: byte offsets of the
+// words holding the side sites; RB: bytes per plane row.
+template <bool LEFT, bool COUNTS, bool LT0, int NWN>
 __device__ __forceinline__ void nib_row(const PassArgs &A, const PhiloxKey &ks,
-                                        const uint8_t *tab, NibWalk &w,
+                                        const uint8_t *tab, NibWalk<NWN> &w,
                                         int32_t xb, int32_t xl, int32_t xr,
                                         int32_t RB, bool more,
                                         uint32_t *lane_hist,
                                         uint32_t &ne_total) {
   const int32_t L = A.L, H = A.H;
-  const uint2 dv = __ldg(reinterpret_cast<const uint2 *>(w.oth_next));
-  const uint32_t Dw[2] = {dv.x, dv.y};
+  uint32_t Dw[NWN];
+  nib_load<NWN, false>(w.oth_next, Dw);
   const uint32_t ew = __ldg(reinterpret_cast<const uint32_t *>(
       w.oth_cur - xb + (LEFT ? xl : xr)));
   uint8_t *own_next = (w.i + 1 == L) ? A.own + xb : w.own_cur + RB;
-  uint32_t Sn[2] = {w.S[0], w.S[1]};
-  if (more) {
-    const uint2 sv = __ldcs(reinterpret_cast<const uint2 *>(own_next));
-    Sn[0] = sv.x;
-    Sn[1] = sv.y;
-  }
+  uint32_t Sn[NWN];
+#pragma unroll
+  for (int k = 0; k < NWN; ++k) Sn[k] = w.S[k];
+  if (more) nib_load<NWN, true>(own_next, Sn);
   const uint32_t *Cw = w.Ce;
-  uint32_t Wd[2];
-  if (LEFT) {  // site x-1: the top nibble of the word before the window
+  uint32_t Wd[NWN];
+  if (LEFT) {  // site x-1: the top nibble of the word before
     Wd[0] = __funnelshift_l(ew, Cw[0], 4);
-    Wd[1] = __funnelshift_l(Cw[0], Cw[1], 4);
-  } else {     // site x+1: the low nibble of the word after it
-    Wd[0] = __funnelshift_r(Cw[0], Cw[1], 4);
-    Wd[1] = __funnelshift_r(Cw[1], ew, 4);
+#pragma unroll
+    for (int k = 1; k < NWN; ++k) Wd[k] = __funnelshift_l(Cw[k - 1], Cw[k], 4);
+  } else {     // site x+1: the low nibble of the word after
+#pragma unroll
+    for (int k = 0; k < NWN - 1; ++k)
+      Wd[k] = __funnelshift_r(Cw[k], Cw[k + 1], 4);
+    Wd[NWN - 1] = __funnelshift_r(Cw[NWN - 1], ew, 4);
   }
   const uint32_t one = A.one;
-  uint32_t Nw[2], ne_acc = 0;
+  uint32_t Nw[NWN], ne_acc = 0;
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < NWN; ++k) {
     const uint4 u0 = philox10(w.g0 + 2u * k, A.t_lo, A.colour, A.t_hi, ks);
     const uint4 u1 =
         philox10(w.g0 + 2u * k + 1u, A.t_lo, A.colour, A.t_hi, ks);
@@ -123,17 +151,18 @@ __device__ __forceinline__ void nib_row(const PassArgs &A, const PhiloxKey &ks,
       ne_acc += (nf & 0x0F0F0F0Fu) + ((nf >> 4) & 0x0F0F0F0Fu);
     }
   }
-  if (COUNTS) ne_total += (ne_acc * 0x01010101u) >> 24;  // <= 64 per byte
-  __stcs(reinterpret_cast<uint2 *>(w.own_cur), make_uint2(Nw[0], Nw[1]));
+  // <= 8 NWN (32) per byte, so the four bytes sum below 256
+  if (COUNTS) ne_total += (ne_acc * 0x01010101u) >> 24;
+  nib_store<NWN>(w.own_cur, Nw);
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < NWN; ++k) {
 #pragma unroll
     for (int b = 0; b < 4; ++b)
       atomicAdd(lane_hist + __byte_perm(Nw[k], 0u, 0x4440u + (uint32_t)b) * 32u,
                 1u);
   }
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < NWN; ++k) {
     w.Up[k] = w.Ce[k];
     w.Ce[k] = Dw[k];
     w.S[k] = Sn[k];
@@ -146,11 +175,11 @@ __device__ __forceinline__ void nib_row(const PassArgs &A, const PhiloxKey &ks,
   w.g0 += (uint32_t)(H >> 2);
 }
 
-// Walks rows [i0, i0 + rows) of the 16-site column starting at site x0 of
-// the plane of colour COLOUR (U4 layout).  lane_hist: per-lane pair bins;
-// COUNTS (black pass): *ne_total receives the unequal (site, neighbour)
-// pairs after the update.
-template <int COLOUR, bool COUNTS, bool LT0>
+// Walks rows [i0, i0 + rows) of the 8 NWN-site column starting at site x0
+// of the plane of colour COLOUR (U4 layout).  lane_hist: per-lane pair
+// bins; COUNTS (black pass): *ne_total receives the unequal (site,
+// neighbour) pairs after the update.
+template <int COLOUR, bool COUNTS, bool LT0, int NWN = 2>
 __device__ __forceinline__ void nib_walk_column(const PassArgs &A,
                                                 const PhiloxKey &ks,
                                                 const uint8_t *tab, int32_t x0,
@@ -159,42 +188,37 @@ __device__ __forceinline__ void nib_walk_column(const PassArgs &A,
                                                 uint32_t *ne_total) {
   const int32_t L = A.L, H = A.H, RB = H / 2, xb = x0 / 2;
   const int32_t xl = (x0 == 0) ? RB - 4 : xb - 4;  // word holding site x0-1
-  const int32_t xr = (x0 + 16 == H) ? 0 : xb + 8;  // word holding x0+16
-  NibWalk w;
+  // word holding site x0 + 8 NWN
+  const int32_t xr = (x0 + 8 * NWN == H) ? 0 : xb + 4 * NWN;
+  NibWalk<NWN> w;
   const int32_t im = (i0 == 0) ? L - 1 : i0 - 1;
   const int32_t ip = (i0 + 1 == L) ? 0 : i0 + 1;
   w.oth_cur = A.other + (int64_t)i0 * RB + xb;
   w.oth_next = A.other + (int64_t)ip * RB + xb;
   w.own_cur = A.own + (int64_t)i0 * RB + xb;
-  const uint2 uv =
-      __ldg(reinterpret_cast<const uint2 *>(A.other + (int64_t)im * RB + xb));
-  const uint2 cv = __ldg(reinterpret_cast<const uint2 *>(w.oth_cur));
-  const uint2 sv = __ldcs(reinterpret_cast<const uint2 *>(w.own_cur));
-  w.Up[0] = uv.x;
-  w.Up[1] = uv.y;
-  w.Ce[0] = cv.x;
-  w.Ce[1] = cv.y;
-  w.S[0] = sv.x;
-  w.S[1] = sv.y;
+  nib_load<NWN, false>(A.other + (int64_t)im * RB + xb, w.Up);
+  nib_load<NWN, false>(w.oth_cur, w.Ce);
+  nib_load<NWN, true>(w.own_cur, w.S);
   w.i = i0;
   w.g0 = (uint32_t)(((int64_t)(i0 + A.grow0) * H + x0) >> 2);
   int32_t r = 0;
   if (((i0 + A.grow0) & 1) == 0) {
     for (; r + 2 <= rows; r += 2) {
-      nib_row<COLOUR == 0, COUNTS, LT0>(A, ks, tab, w, xb, xl, xr, RB, true,
-                                        lane_hist, *ne_total);
-      nib_row<COLOUR == 1, COUNTS, LT0>(A, ks, tab, w, xb, xl, xr, RB,
-                                        r + 2 < rows, lane_hist, *ne_total);
+      nib_row<COLOUR == 0, COUNTS, LT0, NWN>(A, ks, tab, w, xb, xl, xr, RB,
+                                             true, lane_hist, *ne_total);
+      nib_row<COLOUR == 1, COUNTS, LT0, NWN>(A, ks, tab, w, xb, xl, xr, RB,
+                                             r + 2 < rows, lane_hist,
+                                             *ne_total);
     }
   }
   for (; r < rows; ++r) {
     const bool left = ((w.i + A.grow0 + COLOUR) & 1) == 0;
     if (left)
-      nib_row<true, COUNTS, LT0>(A, ks, tab, w, xb, xl, xr, RB, r + 1 < rows,
-                                 lane_hist, *ne_total);
+      nib_row<true, COUNTS, LT0, NWN>(A, ks, tab, w, xb, xl, xr, RB,
+                                      r + 1 < rows, lane_hist, *ne_total);
     else
-      nib_row<false, COUNTS, LT0>(A, ks, tab, w, xb, xl, xr, RB, r + 1 < rows,
-                                  lane_hist, *ne_total);
+      nib_row<false, COUNTS, LT0, NWN>(A, ks, tab, w, xb, xl, xr, RB,
+                                       r + 1 < rows, lane_hist, *ne_total);
   }
 }
 

@@ -208,14 +208,21 @@ __device__ __forceinline__ void hist_word(uint32_t *lane_hist, uint32_t w) {
 }
 
 // Count of bin v summed over the 32 lanes' counters (lane l's counter of
-// bin v at v * 32 + l).  Lane l starts at counter (l + v) mod 32, so when the
-// threads of a warp fold consecutive bins each step's 32 loads hit 32
-// different banks (in lane order they would all hit bank l).
+// bin v at v * 32 + l; s_hist 16-byte aligned).  Read as eight 16-byte
+// chunks, chunk j ^ (v mod 8) at step j: when the threads of a warp fold
+// consecutive bins, the eight lanes of a quarter-warp (one 128-bit
+// wavefront) then hit eight different bank groups (in order they would all
+// hit the same one).
 __device__ __forceinline__ uint32_t bin_sum(const uint32_t *s_hist,
                                             uint32_t v) {
+  const uint4 *row = reinterpret_cast<const uint4 *>(s_hist + v * 32u);
+  const uint32_t rot = v & 7u;
   uint32_t sum = 0;
-#pragma unroll 8
-  for (uint32_t l = 0; l < 32u; ++l) sum += s_hist[v * 32u + ((l + v) & 31u)];
+#pragma unroll
+  for (uint32_t j = 0; j < 8u; ++j) {
+    const uint4 x = row[j ^ rot];
+    sum += x.x + x.y + x.z + x.w;
+  }
   return sum;
 }
 

@@ -214,7 +214,8 @@ def test_mid_config_protocol(start, ladder_dir):
 # ------------------------------------------------------- packed 4-bit layout
 U4_CASES = [(32, 2, 1, 0.44, 30), (96, 9, 0, math.log(4.0), 20),
             (160, 16, 1, 1.3, 15), (544, 15, 1, 1.1, 8), (128, 9, 0, 40.0, 4),
-            (128, 6, 1, 0.0, 4), (4160, 9, 1, workloads.beta_at(9, 1.0), 2)]
+            (128, 6, 1, 0.0, 4), (64, 9, 1, 1.1, 10),
+            (4160, 9, 1, workloads.beta_at(9, 1.0), 2)]
 
 
 @pytest.mark.parametrize("L,q,start,beta,sweeps", U4_CASES)
