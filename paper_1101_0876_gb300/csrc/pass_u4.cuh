@@ -126,7 +126,11 @@ __device__ __forceinline__ void nib_row(const PassArgs &A, const PhiloxKey &ks,
     for (int j = 0; j < 8; ++j) {
       const uint64_t r = (uint64_t)uw[j] * A.q;
       a[j] = (uint32_t)r;
-      P |= (uint32_t)(r >> 32) << (4 * j);
+      // proposal into nibble j: a multiply-add with the run-time one (the
+      // fields are disjoint), on the FMA-heavy pipe (1.117 against 1.147 ps
+      // per update at L = 32768 with shifts and ORs; for the byte walk's
+      // pack4 the byte permutes stay faster, 1.194 against 1.236)
+      P = (uint32_t)(r >> 32) * (one << (4 * j)) + P;
     }
     const uint32_t S = w.S[k];
     const uint32_t Y = nib_ne(S, w.Up[k], one) + nib_ne(S, Dw[k], one) +
