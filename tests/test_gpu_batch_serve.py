@@ -36,6 +36,8 @@ MIX = [  # L, q, start, seed, beta
     (288, 9, 1, 8, 0.0),
     (96, 9, 0, 9, 40.0),
     (544, 15, 1, 10, workloads.beta_at(15, 1.0)),
+    (128, 9, 1, 11, 40.0),              # 32-site walks, acceptance rule LT0
+    (320, 6, 0, 12, workloads.beta_at(6, 1.0)),  # 32-site walks, 5 per row
 ]
 
 
