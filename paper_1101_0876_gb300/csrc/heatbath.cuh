@@ -120,6 +120,25 @@ __device__ __forceinline__ uint32_t hb_put(uint32_t x, uint32_t acc,
     return x * (one << (TO - FROM)) + acc;
 }
 
+// [a == b] for every byte (spins < 2^QB), as bit T of the byte, added to
+// acc (whose bit T is clear).  For x = a ^ b < 2^QB and T >= QB, bit T of
+// x + 2^T - 1 is [x != 0] and the sum stays inside the byte (at most
+// 2^QB + 2^T - 2 < 2^(T+1) <= 256), so the test lands at bit T directly
+// and one logic op masks, inverts and adds it; for T < QB it is taken at
+// bit QB and moved down (hb_put).
+template <int QB, int T>
+__device__ __forceinline__ uint32_t hb_eq_at(uint32_t a, uint32_t b,
+                                             uint32_t acc, uint32_t one) {
+  if constexpr (T >= QB) {
+    constexpr uint32_t K = 0x01010101u * ((1u << T) - 1u);
+    constexpr uint32_t M = 0x01010101u * (1u << T);
+    return (~((a ^ b) * one + K) & M) | acc;
+  } else {
+    constexpr uint32_t K = Swar<QB>::K, M = Swar<QB>::M;
+    return hb_put<QB, T>(~((a ^ b) * one + K) & M, acc, one);
+  }
+}
+
 // The four sites of one word at once (spins < 2^QB, QB <= 6): the same
 // rule as hb_site, with the six neighbour equalities done per byte on whole
 // words and packed into the four sites' pattern codes, the interval bounds
@@ -139,27 +158,22 @@ __device__ __forceinline__ uint32_t hb_word(uint32_t U, uint32_t D,
                                             const uint8_t *ent, uint32_t m,
                                             uint32_t qm, uint32_t one) {
   static_assert(QB <= 6, "byte sums below need spins < 64");
-  constexpr uint32_t K = Swar<QB>::K, M = Swar<QB>::M;
-  // 2^QB per byte where two neighbours are equal
-  const uint32_t E01 = ~((U ^ D) * one + K) & M;
-  const uint32_t E02 = ~((U ^ Lw) * one + K) & M;
-  const uint32_t E03 = ~((U ^ Rw) * one + K) & M;
-  const uint32_t E12 = ~((D ^ Lw) * one + K) & M;
-  const uint32_t E13 = ~((D ^ Rw) * one + K) & M;
-  const uint32_t E23 = ~((Lw ^ Rw) * one + K) & M;
-  // pattern code per byte (bit order of the table)
-  uint32_t CODE = hb_put<QB, 0>(E01, 0u, one);
-  CODE = hb_put<QB, 1>(E02, CODE, one);
-  CODE = hb_put<QB, 2>(E03, CODE, one);
-  CODE = hb_put<QB, 3>(E12, CODE, one);
-  CODE = hb_put<QB, 4>(E13, CODE, one);
-  CODE = hb_put<QB, 5>(E23, CODE, one);
+  // four times the pattern code per byte: the six equalities at bits 2..7
+  // in the table's bit order, so that a site's code byte times 32 is its
+  // entry's offset (128 bytes per code); the tests whose bit is at or above
+  // QB need no move
+  uint32_t CODE = hb_eq_at<QB, 2>(U, D, 0u, one);
+  CODE = hb_eq_at<QB, 3>(U, Lw, CODE, one);
+  CODE = hb_eq_at<QB, 4>(U, Rw, CODE, one);
+  CODE = hb_eq_at<QB, 5>(D, Lw, CODE, one);
+  CODE = hb_eq_at<QB, 6>(D, Rw, CODE, one);
+  CODE = hb_eq_at<QB, 7>(Lw, Rw, CODE, one);
   const uint32_t neg = 0u - one;  // -1 at run time
   uint32_t N = 0;
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     const uint4 sb =
-        *reinterpret_cast<const uint4 *>(ent + hb_byte(CODE, b) * 128u);
+        *reinterpret_cast<const uint4 *>(ent + hb_byte(CODE, b) * 32u);
     const uint32_t r = __umulhi(uw[b], sb.w * one + qm);
     // whole-word candidates, each holding site b's answer in byte b: first
     // the state among the bases (< q when r >= s4; when r < s4 a neighbour

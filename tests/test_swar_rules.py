@@ -125,22 +125,22 @@ def _hb_word(QB, U, D, Lw, Rw, uw, tab, m):
     """hb_word: new spins (word) of four sites from their neighbour words
     and Philox words uw (n, 4)."""
     u = np.uint64
-    K = u(0x01010101 * ((1 << QB) - 1))
-    M = u(0x01010101 * (1 << QB))
 
-    def eq(a, b):
-        return ((((a ^ b) + K) & u(M32)) ^ u(M32)) & M
+    def eq_at(a, b, t):
+        """[a == b] per byte at bit t: straight from bit t of x + 2^t - 1
+        when t >= QB, else from bit QB moved down."""
+        p = max(t, QB)
+        K, M = u(0x01010101 * ((1 << p) - 1)), u(0x01010101 * (1 << p))
+        e = ((((a ^ b) + K) & u(M32)) ^ u(M32)) & M
+        return e >> u(p - t)
 
-    def mv(x, to):
-        return x >> u(QB - to) if QB >= to else (x << u(to - QB)) & u(M32)
-
-    E01, E02, E03 = eq(U, D), eq(U, Lw), eq(U, Rw)
-    E12, E13, E23 = eq(D, Lw), eq(D, Rw), eq(Lw, Rw)
-    CODE = mv(E01, 0) | mv(E02, 1) | mv(E03, 2) | mv(E12, 3) | mv(E13, 4) | \
-        mv(E23, 5)
+    # four times the pattern code per byte: the equalities at bits 2..7
+    CODE = eq_at(U, D, 2) | eq_at(U, Lw, 3) | eq_at(U, Rw, 4) | \
+        eq_at(D, Lw, 5) | eq_at(D, Rw, 6) | eq_at(Lw, Rw, 7)
+    assert not (CODE & u(0x03030303)).any()
     N = np.zeros((U.size, 4), dtype=np.uint64)
     for b in range(4):
-        e = tab[_byte(CODE, b).astype(np.int64)]
+        e = tab[(_byte(CODE, b) >> u(2)).astype(np.int64)]
         r = (uw[:, b].astype(np.uint64) * e[:, 4]) >> u(32)
         n = (((r - e[:, 3]) & u(M32)) >> u(m)) & u(0xFF)
         # later (lower) bounds overwrite: the first interval holding r wins
