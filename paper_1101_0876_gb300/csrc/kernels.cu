@@ -11,10 +11,12 @@ namespace potts {
 
 // ------------------------------------------------------------ the pass
 // Grid: (gx, gy) CTAs of 128 threads.  Thread t of CTA (bx, by) owns chunk
-// bx*CX + t%CX (16 bytes) and rows starting at (by*RG + t/CX)*TR.
+// bx*CX + t%CX (16 or 32 sites) and rows starting at (by*RG + t/CX)*TR.
 // Each pass histograms the sites it updated (their final values for this
-// sweep); the black pass also reduces the satisfied-bond count of the black
-// sites against the final white spins, which counts every bond once
+// sweep), except with the cross-plane pair bins (XP), where the black pass
+// histograms both planes' sites; the black pass also reduces the
+// satisfied-bond count of the black sites against the final white spins,
+// which counts every bond once
 // (Sec. 3.4: per-block energies and state counters, here summed with warp
 // shuffles and shared atomics and added with one 64-bit atomic per
 // non-empty bin per CTA, without a second kernel or a CPU-side sum).

@@ -9,11 +9,11 @@
 // row i at x, and row i at x-1 when (i + c) is even, x+1 when it is odd
 // (all indices periodic).
 //
-// Work unit.  One thread owns 16 consecutive bytes (16 sites) of a row and
-// walks down `rows` consecutive rows, keeping the three other-plane rows it
-// needs (i-1, i, i+1) in registers, so each other-plane row is fetched from
-// memory once per walk.  The one byte that lies outside the 16-byte window
-// (x-1 or x+16) comes from a 4-byte load that hits L1/L2.
+// Work unit.  One thread owns 4 NW consecutive bytes (16 or 32 sites) of a
+// row and walks down `rows` consecutive rows, keeping the three other-plane
+// rows it needs (i-1, i, i+1) in registers, so each other-plane row is
+// fetched from memory once per walk.  The one byte that lies outside the
+// window (x-1 or x + 4 NW) comes from a 4-byte load that hits L1/L2.
 //
 // Arithmetic is byte-SIMD on 32-bit words (4 sites per word):
 //   - neighbour compares: for x = a ^ b per byte, "x != 0" is read from one
@@ -244,10 +244,12 @@ __device__ __forceinline__ void hist_cross(uint32_t *lane_hist, uint32_t nw,
 }
 
 // ------------------------------------------------------- plane layouts
-// U8: one byte per spin, 16 sites = 16 bytes per thread-row.
+// U8: one byte per spin, 16 sites = 16 bytes per vector (one or two per
+// thread-row).
 // U4: two spins per byte (site 2b in the low nibble of byte b, site 2b+1 in
 // the high one), 16 sites = 8 bytes, unpacked to the same four byte-words
-// as U8 so that the arithmetic is shared.
+// as U8 so that the arithmetic is shared (the heat-bath walk; the
+// Metropolis pass computes on the nibbles themselves, pass_u4.cuh).
 enum { kLayoutU8 = 1, kLayoutU4 = 2 };
 
 // nibbles n0..n7 (sites 0..7) -> bytes [s0..s3], [s4..s7]
