@@ -35,9 +35,10 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_HB_MINB)
   __shared__ uint32_t s_sat;
   __shared__ uint32_t s_fold[16];
   const uint32_t tid = threadIdx.x;
+  constexpr uint32_t STRIDE = XP ? kPairStride : 32u;  // words per bin
   const uint32_t bins = PBINS ? (uint32_t)kHbPairBins : A.hist_bins;
   if (HIST)
-    for (uint32_t v = tid; v < bins * 32u; v += kPassThreads) s_hist[v] = 0;
+    for (uint32_t v = tid; v < bins * STRIDE; v += kPassThreads) s_hist[v] = 0;
   if (tid < 16) s_fold[tid] = 0;
   if (tid == 0) s_sat = 0;
   hb_build_table(s_W, T.W, tid);  // ends with a barrier
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_HB_MINB)
   if (!HIST) return;
   if (PBINS) {
     for (uint32_t p = tid; p < (uint32_t)kHbPairBins; p += kPassThreads) {
-      const uint32_t sum = bin_sum(s_hist, p);
+      const uint32_t sum = bin_sum(s_hist, p, STRIDE);
       if (sum) {
         atomicAdd(&s_fold[p & 15u], sum);
         atomicAdd(&s_fold[p >> 4], sum);
@@ -92,7 +93,9 @@ cudaError_t launch_hb_c(const PassArgs &A, const HeatTable &T,
                         cudaStream_t st) {
   dim3 grid(G.gx, G.gy), block(kPassThreads);
   const size_t bins = (PAIRS || XP) ? kHbPairBins : A.hist_bins;
-  const size_t smem = (XP && COLOUR == 0) ? 0 : bins * 32u * sizeof(uint32_t);
+  const size_t smem = (XP && COLOUR == 0)
+                          ? 0
+                          : bins * (XP ? kPairStride : 32u) * sizeof(uint32_t);
   return launch_pdl(hb_pass_kernel<QB, COLOUR, PAIRS, LAY, XP>, grid, block,
                     smem, st, A, T, G, rec);
 }

@@ -254,7 +254,8 @@ __device__ __forceinline__ void hb_row(const PassArgs &A, const PhiloxKey &ks,
   if constexpr (XP) {
     if (COUNTS) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) hist_cross(lane_hist, Nw[k], Cw[k], 1u);
+      for (int k = 0; k < 4; ++k)
+        hist_cross(lane_hist - (threadIdx.x & 31u), Nw[k], Cw[k], 1u);
     }
   } else {
 #pragma unroll

@@ -93,11 +93,21 @@ __device__ __forceinline__ void pdl_release_next() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Opts `kernel` in to `smem` bytes of dynamic shared memory on the current
+// device where that is above the 48 KB needing no opt-in (once per kernel,
+// device and size; thread-safe).
+cudaError_t allow_dynamic_smem(const void *kernel, size_t smem);
+
 // Launches kernel<<<grid, block, smem, st>>>(args...) with the programmatic
 // stream serialization attribute.
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block,
                        size_t smem, cudaStream_t st, Args &&...args) {
+  if (smem > 48u * 1024u) {
+    const cudaError_t e =
+        allow_dynamic_smem(reinterpret_cast<const void *>(kernel), smem);
+    if (e != cudaSuccess) return e;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;

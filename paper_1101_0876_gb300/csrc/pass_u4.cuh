@@ -162,8 +162,7 @@ __device__ __forceinline__ void nib_row(const PassArgs &A, const PhiloxKey &ks,
   for (int k = 0; k < NWN; ++k) {
 #pragma unroll
     for (int b = 0; b < 4; ++b)
-      atomicAdd(lane_hist + __byte_perm(Nw[k], 0u, 0x4440u + (uint32_t)b) * 32u,
-                1u);
+      pair_count(lane_hist - (threadIdx.x & 31u), Nw[k], b);
   }
 #pragma unroll
   for (int k = 0; k < NWN; ++k) {

@@ -208,14 +208,15 @@ __device__ __forceinline__ void hist_word(uint32_t *lane_hist, uint32_t w) {
 }
 
 // Count of bin v summed over the 32 lanes' counters (lane l's counter of
-// bin v at v * 32 + l; s_hist 16-byte aligned).  Read as eight 16-byte
+// bin v at v * stride + l; s_hist 16-byte aligned).  Read as eight 16-byte
 // chunks, chunk j ^ (v mod 8) at step j: when the threads of a warp fold
 // consecutive bins, the eight lanes of a quarter-warp (one 128-bit
 // wavefront) then hit eight different bank groups (in order they would all
 // hit the same one).
 __device__ __forceinline__ uint32_t bin_sum(const uint32_t *s_hist,
-                                            uint32_t v) {
-  const uint4 *row = reinterpret_cast<const uint4 *>(s_hist + v * 32u);
+                                            uint32_t v,
+                                            uint32_t stride = 32u) {
+  const uint4 *row = reinterpret_cast<const uint4 *>(s_hist + v * stride);
   const uint32_t rot = v & 7u;
   uint32_t sum = 0;
 #pragma unroll
@@ -224,6 +225,24 @@ __device__ __forceinline__ uint32_t bin_sum(const uint32_t *s_hist,
     sum += x.x + x.y + x.z + x.w;
   }
   return sum;
+}
+
+// Pair-bin counters (256 bins of two spins below 16): lane l's counter of
+// bin p at word p * kPairStride + l.  The 64-word stride lets one byte
+// permute form a counter's byte offset from the pair byte and the lane (the
+// bin in bits 8..15, 4 l in bits 0..6); a 32-word stride needs a
+// shift-and-add more per count.
+constexpr uint32_t kPairStride = 64;
+
+// Counts pair bin (byte b of t) in the calling lane's counters; s_hist: the
+// CTA's counters (kPairStride words a bin).
+__device__ __forceinline__ void pair_count(uint32_t *s_hist, uint32_t t,
+                                           int b) {
+  const uint32_t lane4 = (threadIdx.x & 31u) << 2;
+  const uint32_t off = __byte_perm(t, lane4, 0x5504u | ((uint32_t)b << 4));
+  atomicAdd(reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(s_hist) +
+                                         off),
+            1u);
 }
 
 // Histogram of one black word's new spins paired with the white spins at
@@ -235,12 +254,12 @@ __device__ __forceinline__ uint32_t bin_sum(const uint32_t *s_hist,
 // not check) can only scramble the bins, never leave them.  one: 1, as a
 // literal (the pair forms on the ALU pipe) or the run-time 1 of PassArgs
 // (a multiply-add on the FMA-heavy pipe).
-__device__ __forceinline__ void hist_cross(uint32_t *lane_hist, uint32_t nw,
+// s_hist: the CTA's pair-bin counters (pair_count).
+__device__ __forceinline__ void hist_cross(uint32_t *s_hist, uint32_t nw,
                                            uint32_t cw, uint32_t one) {
   const uint32_t t = cw * (one << 4) + nw;
 #pragma unroll
-  for (int b = 0; b < 4; ++b)
-    atomicAdd(lane_hist + __byte_perm(t, 0u, 0x4440u + (uint32_t)b) * 32u, 1u);
+  for (int b = 0; b < 4; ++b) pair_count(s_hist, t, b);
 }
 
 // ------------------------------------------------------- plane layouts
@@ -412,7 +431,8 @@ __device__ __forceinline__ void do_row(const PassArgs &A, const PhiloxKey &ks,
   if constexpr (XP) {
     if (COUNTS) {
 #pragma unroll
-      for (int k = 0; k < NW; ++k) hist_cross(lane_hist, Nw[k], Cw[k], 1u);
+      for (int k = 0; k < NW; ++k)
+        hist_cross(lane_hist - (threadIdx.x & 31u), Nw[k], Cw[k], 1u);
     }
   } else {
 #pragma unroll
