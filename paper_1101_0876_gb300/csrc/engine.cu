@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kPassThreads,
     for (uint32_t i = tid; i < (uint32_t)kTabWords; i += kPassThreads)
       s_tab[i] = (i % 4u == 0 && i / 4u < 9u) ? sd.tab[i / 4u] : 0u;
   }
-  for (uint32_t v = tid; v < q * 32u; v += kPassThreads) s_hist[v] = 0;
+  for (uint32_t v = tid; v < q * kBinStride; v += kPassThreads) s_hist[v] = 0;
   if (tid == 0) s_sat = 0;
   if (KIND == kKindHB)
     hb_build_table(s_tab, sd.tab, tid);  // W[0..7]; barrier
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kPassThreads,
   __syncthreads();
   if (COUNTS && tid == 0 && s_sat) atomicAdd(rec, (unsigned long long)s_sat);
   for (uint32_t v = tid; v < q; v += kPassThreads) {
-    const uint32_t sum = bin_sum(s_hist, v);
+    const uint32_t sum = bin_sum(s_hist, v, kBinStride);
     if (sum) atomicAdd(rec + 1 + v, (unsigned long long)sum);
   }
 }
@@ -423,7 +423,8 @@ int Engine::launch_all(Slot &sl, int32_t kmax) {
     for (int c = 0; c < 2; ++c)
       for (const Unit &u : units_)
         POTTS_CK(launch_batch_pass(*u.P, u.kind, sl.d_step, c, s,
-                                   (size_t)u.maxq * 32 * sizeof(uint32_t),
+                                   (size_t)u.maxq * kBinStride *
+                                       sizeof(uint32_t),
                                    u.lane ? aux_[u.lane - 1] : st_));
   for (int l = 1; l < lanes_; ++l) {  // join
     POTTS_CK(cudaEventRecord(join_[l - 1], aux_[l - 1]));

@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kFThreads, 3)
     *reinterpret_cast<uint4 *>(own) = make_uint4(N[0], N[1], N[2], N[3]);
     if (rr >= 1 && rr <= kFR && cc >= 1 && cc <= kFTW) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) hist_word<PAIRS>(lh, N[k]);
+      for (int k = 0; k < 4; ++k) hist_word<PAIRS, false>(lh, N[k]);
     }
   }
   __syncthreads();
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kFThreads, 3)
     items += 1;
     *reinterpret_cast<uint4 *>(own) = make_uint4(N[0], N[1], N[2], N[3]);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) hist_word<PAIRS>(lh, N[k]);
+    for (int k = 0; k < 4; ++k) hist_word<PAIRS, false>(lh, N[k]);
   }
   pdl_release_next();
   // the threads' shared-memory writes, visible to the copy engine
@@ -330,12 +330,7 @@ cudaError_t launch_fused_k(const uint8_t *white, const uint8_t *black,
                            int32_t H, uint32_t q, uint64_t t, uint64_t seed,
                            const AcceptTable &T, unsigned long long *rec,
                            cudaStream_t st) {
-  // set on every launch (a host-side call): handles may run on several
-  // devices and threads
-  const cudaError_t e = cudaFuncSetAttribute(
-      fused_sweep_kernel<QB, PAIRS, LT0>,
-      cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmemMax);
-  if (e != cudaSuccess) return e;
+  static_assert(kFSmemMax <= kDynSmemCap, "launch_pdl's opt-in cap");
   const dim3 grid((unsigned)(H / 16 / kFTW), (unsigned)(L / kFR));
   const size_t smem = (size_t)kWBytes + kBBytes +
                       (size_t)(PAIRS ? kFPairBins : q) * 32u * 4u;

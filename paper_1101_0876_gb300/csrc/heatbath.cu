@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_HB_MINB)
   __shared__ uint32_t s_sat;
   __shared__ uint32_t s_fold[16];
   const uint32_t tid = threadIdx.x;
-  constexpr uint32_t STRIDE = XP ? kPairStride : 32u;  // words per bin
+  constexpr uint32_t STRIDE = kBinStride;  // words per bin (bin_count)
   const uint32_t bins = PBINS ? (uint32_t)kHbPairBins : A.hist_bins;
   if (HIST)
     for (uint32_t v = tid; v < bins * STRIDE; v += kPassThreads) s_hist[v] = 0;
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_HB_MINB)
       atomicAdd(rec + 1 + tid, (unsigned long long)s_fold[tid]);
   } else {
     for (uint32_t v = tid; v < A.q; v += kPassThreads) {
-      const uint32_t sum = bin_sum(s_hist, v);
+      const uint32_t sum = bin_sum(s_hist, v, STRIDE);
       if (sum) atomicAdd(rec + 1 + v, (unsigned long long)sum);
     }
   }
@@ -95,7 +95,7 @@ cudaError_t launch_hb_c(const PassArgs &A, const HeatTable &T,
   const size_t bins = (PAIRS || XP) ? kHbPairBins : A.hist_bins;
   const size_t smem = (XP && COLOUR == 0)
                           ? 0
-                          : bins * (XP ? kPairStride : 32u) * sizeof(uint32_t);
+                          : bins * kBinStride * sizeof(uint32_t);
   return launch_pdl(hb_pass_kernel<QB, COLOUR, PAIRS, LAY, XP>, grid, block,
                     smem, st, A, T, G, rec);
 }

@@ -93,9 +93,11 @@ __device__ __forceinline__ void pdl_release_next() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Opts `kernel` in to `smem` bytes of dynamic shared memory on the current
-// device where that is above the 48 KB needing no opt-in (once per kernel,
-// device and size; thread-safe).
+// Opts `kernel` in to dynamic shared memory above the 48 KB that need no
+// opt-in, up to kDynSmemCap (the largest any kernel here asks for: the fused
+// sweep's tiles and pair bins), in the current context; launch_pdl calls it
+// before each launch of more than 48 KB.  smem above the cap: invalid value.
+constexpr int kDynSmemCap = 72 * 1024;
 cudaError_t allow_dynamic_smem(const void *kernel, size_t smem);
 
 // Launches kernel<<<grid, block, smem, st>>>(args...) with the programmatic

@@ -7,10 +7,6 @@
 #include "internal.cuh"
 #include "pass_u4.cuh"
 
-#include <mutex>
-#include <set>
-#include <tuple>
-
 namespace potts {
 
 // ------------------------------------------------------------ the pass
@@ -34,18 +30,14 @@ constexpr int kMinb32 = 3, kMinbNib = 4;
 // XP (q <= 16): the histogram of both planes in (black, white) pair bins,
 // kept by the black pass alone (hist_cross); the white pass keeps none.
 cudaError_t allow_dynamic_smem(const void *kernel, size_t smem) {
-  static std::mutex mu;
-  static std::set<std::tuple<const void *, int, size_t>> done;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  std::lock_guard<std::mutex> lock(mu);
-  const auto key = std::make_tuple(kernel, dev, smem);
-  if (done.count(key)) return cudaSuccess;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-  if (e == cudaSuccess) done.insert(key);
-  return e;
+  // Set before every such launch, and always to the same cap: the attribute
+  // belongs to the kernel in the current context, and one value for every
+  // launch keeps threads that launch the same kernel with different sizes
+  // from lowering it under each other (a cache keyed by size did exactly
+  // that: a later, larger launch then failed).
+  if (smem > (size_t)kDynSmemCap) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(
+      kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemCap);
 }
 
 template <int QB, int COLOUR, bool PAIRS, bool LT0, int LAY, int NW,
@@ -62,8 +54,7 @@ __global__ void __launch_bounds__(kPassThreads,
   __shared__ uint32_t s_sat;
   __shared__ uint32_t s_fold[16];
   const uint32_t tid = threadIdx.x;
-  // words per bin: pair_count's layout for the cross-plane pairs
-  constexpr uint32_t STRIDE = XP ? kPairStride : 32u;
+  constexpr uint32_t STRIDE = kBinStride;  // words per bin (bin_count)
   const uint32_t bins = PBINS ? (uint32_t)kPairBins : A.hist_bins;
   for (uint32_t i = tid; i < (uint32_t)kTabWords; i += kPassThreads)
     s_tab[i] = (i % 4u == 0 && i / 4u < 9u) ? Tin.tab[i / 4u] : 0u;
@@ -113,7 +104,7 @@ __global__ void __launch_bounds__(kPassThreads,
       atomicAdd(rec + 1 + tid, (unsigned long long)s_fold[tid]);
   } else {
     for (uint32_t v = tid; v < A.q; v += kPassThreads) {
-      const uint32_t sum = bin_sum(s_hist, v);
+      const uint32_t sum = bin_sum(s_hist, v, STRIDE);
       if (sum) atomicAdd(rec + 1 + v, (unsigned long long)sum);
     }
   }
@@ -128,14 +119,14 @@ __global__ void __launch_bounds__(kPassThreads, NWN == 4 ? kMinb32 : kMinbNib)
                    unsigned long long *rec) {
   constexpr bool COUNTS = COLOUR == 1;
   constexpr int32_t SITES = 8 * NWN;
-  extern __shared__ __align__(16) uint32_t s_hist[];  // 256 pair bins, pair_count
+  extern __shared__ __align__(16) uint32_t s_hist[];  // 256 pair bins, bin_count
   __shared__ __align__(16) uint32_t s_tab[kTabWords];
   __shared__ uint32_t s_sat;
   __shared__ uint32_t s_fold[16];
   const uint32_t tid = threadIdx.x;
   for (uint32_t i = tid; i < (uint32_t)kTabWords; i += kPassThreads)
     s_tab[i] = (i % 4u == 0 && i / 4u < 9u) ? Tin.tab[i / 4u] : 0u;
-  for (uint32_t v = tid; v < (uint32_t)kPairBins * kPairStride;
+  for (uint32_t v = tid; v < (uint32_t)kPairBins * kBinStride;
        v += kPassThreads)
     s_hist[v] = 0;
   if (tid < 16) s_fold[tid] = 0;
@@ -168,7 +159,7 @@ __global__ void __launch_bounds__(kPassThreads, NWN == 4 ? kMinb32 : kMinbNib)
   __syncthreads();
   if (COUNTS && tid == 0 && s_sat) atomicAdd(rec, (unsigned long long)s_sat);
   for (uint32_t p = tid; p < (uint32_t)kPairBins; p += kPassThreads) {
-    const uint32_t sum = bin_sum(s_hist, p, kPairStride);
+    const uint32_t sum = bin_sum(s_hist, p, kBinStride);
     if (sum) {
       atomicAdd(&s_fold[p & 15u], sum);
       atomicAdd(&s_fold[p >> 4], sum);
@@ -188,7 +179,7 @@ static cudaError_t launch_c(const PassArgs &A, const AcceptTable &T,
   const size_t bins = (PAIRS || XP) ? kPairBins : A.hist_bins;
   const size_t smem = (XP && COLOUR == 0)
                           ? 0
-                          : bins * (XP ? kPairStride : 32u) * sizeof(uint32_t);
+                          : bins * kBinStride * sizeof(uint32_t);
   if (T.rule_lt0)
     return launch_pdl(pass_kernel<QB, COLOUR, PAIRS, true, LAY, NW, XP>, grid,
                       block, smem, st, A, T, G, rec);
@@ -223,7 +214,7 @@ static cudaError_t launch_u4_n(const PassArgs &A, const AcceptTable &T,
                                const TileGeom &G, unsigned long long *rec,
                                cudaStream_t st) {
   dim3 grid(G.gx, G.gy), block(kPassThreads);
-  const size_t smem = (size_t)kPairBins * kPairStride * sizeof(uint32_t);
+  const size_t smem = (size_t)kPairBins * kBinStride * sizeof(uint32_t);
   if (T.rule_lt0)
     return A.colour ? launch_pdl(pass_u4_kernel<1, true, NWN>, grid, block,
                                  smem, st, A, T, G, rec)
@@ -450,8 +441,8 @@ __global__ void recount_kernel(const uint8_t *white, const uint8_t *black,
       const uint32_t n16 = ne16_sum4<8>(Sw[k] ^ Uw[k], Sw[k] ^ Dw[k],
                                         Sw[k] ^ Cw[k], Sw[k] ^ Wd[k]);
       ne += ((n16 >> 4) * 0x01010101u) >> 24;
-      hist_word<false>(s_hist + (tid & 31u), Sw[k]);
-      hist_word<false>(s_hist + (tid & 31u), Cw[k]);
+      hist_word<false, false>(s_hist + (tid & 31u), Sw[k]);
+      hist_word<false, false>(s_hist + (tid & 31u), Cw[k]);
     }
     sat = 64u - ne;
   }

@@ -162,7 +162,7 @@ __device__ __forceinline__ void nib_row(const PassArgs &A, const PhiloxKey &ks,
   for (int k = 0; k < NWN; ++k) {
 #pragma unroll
     for (int b = 0; b < 4; ++b)
-      pair_count(lane_hist - (threadIdx.x & 31u), Nw[k], b);
+      bin_count(lane_hist - (threadIdx.x & 31u), Nw[k], b);
   }
 #pragma unroll
   for (int k = 0; k < NWN; ++k) {

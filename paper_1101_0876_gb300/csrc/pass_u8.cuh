@@ -189,21 +189,50 @@ __device__ __forceinline__ uint32_t pack4(uint32_t p0, uint32_t p1,
   return __byte_perm(lo, hi, 0x5410u);
 }
 
+// Per-lane histogram counters: lane l's counter of bin p at word
+// p * kBinStride + l.  The 64-word stride lets one byte permute form a
+// counter's byte offset from the bin byte and the lane (the bin in bits
+// 8..15, 4 l in bits 0..6); a 32-word stride needs a shift-and-add more per
+// count.
+constexpr uint32_t kBinStride = 64;
+
+// Counts bin (byte b of t) in the calling lane's counters; s_hist: the CTA's
+// counters (kBinStride words a bin).
+__device__ __forceinline__ void bin_count(uint32_t *s_hist, uint32_t t,
+                                          int b) {
+  const uint32_t lane4 = (threadIdx.x & 31u) << 2;
+  const uint32_t off = __byte_perm(t, lane4, 0x5504u | ((uint32_t)b << 4));
+  atomicAdd(reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(s_hist) +
+                                         off),
+            1u);
+}
+
 // Histogram of the four spins of w into per-lane shared counters.
 // PAIRS (q <= 16): the two nibble-sized spins of sites (0,1) and (2,3) form
 // one 8-bit bin each, so a word costs two shared atomics; the pair bins are
-// folded back to states at the end of the CTA.
-template <bool PAIRS>
+// folded back to states at the end of the CTA.  WIDE: the kBinStride layout
+// (bin_count), else 32 words a bin (lane_hist + 32 bin).
+template <bool PAIRS, bool WIDE = true>
 __device__ __forceinline__ void hist_word(uint32_t *lane_hist, uint32_t w) {
   if (PAIRS) {
     const uint32_t t = w + __umulhi(w, 1u << 28);  // byte0 = v0 | v1 << 4
-    atomicAdd(lane_hist + (t & 0xFFu) * 32u, 1u);
-    atomicAdd(lane_hist + __byte_perm(t, 0u, 0x4442u) * 32u, 1u);
+    if (WIDE) {
+      uint32_t *s_hist = lane_hist - (threadIdx.x & 31u);
+      bin_count(s_hist, t, 0);
+      bin_count(s_hist, t, 2);
+    } else {
+      atomicAdd(lane_hist + (t & 0xFFu) * 32u, 1u);
+      atomicAdd(lane_hist + __byte_perm(t, 0u, 0x4442u) * 32u, 1u);
+    }
   } else {
 #pragma unroll
-    for (int b = 0; b < 4; ++b)
-      atomicAdd(lane_hist + __byte_perm(w, 0u, 0x4440u + (uint32_t)b) * 32u,
-                1u);
+    for (int b = 0; b < 4; ++b) {
+      if (WIDE)
+        bin_count(lane_hist - (threadIdx.x & 31u), w, b);
+      else
+        atomicAdd(lane_hist + __byte_perm(w, 0u, 0x4440u + (uint32_t)b) * 32u,
+                  1u);
+    }
   }
 }
 
@@ -227,24 +256,6 @@ __device__ __forceinline__ uint32_t bin_sum(const uint32_t *s_hist,
   return sum;
 }
 
-// Pair-bin counters (256 bins of two spins below 16): lane l's counter of
-// bin p at word p * kPairStride + l.  The 64-word stride lets one byte
-// permute form a counter's byte offset from the pair byte and the lane (the
-// bin in bits 8..15, 4 l in bits 0..6); a 32-word stride needs a
-// shift-and-add more per count.
-constexpr uint32_t kPairStride = 64;
-
-// Counts pair bin (byte b of t) in the calling lane's counters; s_hist: the
-// CTA's counters (kPairStride words a bin).
-__device__ __forceinline__ void pair_count(uint32_t *s_hist, uint32_t t,
-                                           int b) {
-  const uint32_t lane4 = (threadIdx.x & 31u) << 2;
-  const uint32_t off = __byte_perm(t, lane4, 0x5504u | ((uint32_t)b << 4));
-  atomicAdd(reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(s_hist) +
-                                         off),
-            1u);
-}
-
 // Histogram of one black word's new spins paired with the white spins at
 // the same plane position (q <= 16): byte b of nw + (cw << 4) is the bin
 // (black spin, white spin), so four shared atomics count eight sites and
@@ -254,12 +265,12 @@ __device__ __forceinline__ void pair_count(uint32_t *s_hist, uint32_t t,
 // not check) can only scramble the bins, never leave them.  one: 1, as a
 // literal (the pair forms on the ALU pipe) or the run-time 1 of PassArgs
 // (a multiply-add on the FMA-heavy pipe).
-// s_hist: the CTA's pair-bin counters (pair_count).
+// s_hist: the CTA's counters (bin_count).
 __device__ __forceinline__ void hist_cross(uint32_t *s_hist, uint32_t nw,
                                            uint32_t cw, uint32_t one) {
   const uint32_t t = cw * (one << 4) + nw;
 #pragma unroll
-  for (int b = 0; b < 4; ++b) pair_count(s_hist, t, b);
+  for (int b = 0; b < 4; ++b) bin_count(s_hist, t, b);
 }
 
 // ------------------------------------------------------- plane layouts
