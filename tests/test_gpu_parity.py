@@ -255,3 +255,16 @@ def test_u4_paper_scale_sampled():
                           oracle.sweep_sites(pre, q, seed, t, beta, idx))
     B, hist = oracle.recount(g.spins(), q)
     assert int(rec[0, 0]) == B and np.array_equal(rec[0, 1:], hist)
+
+
+def test_shared_memory_opt_in_across_sizes():
+    """Passes whose per-lane counters need more than 48 KB of shared memory
+    (q = 200 and q = 256: 200 and 256 bins of 256 bytes) alternating in one
+    process with each other and with a small one: every launch opts in, and
+    records and spins stay equal to the oracle's."""
+    for L, q in [(64, 200), (64, 256), (96, 200), (64, 9), (64, 256)]:
+        seed, beta = 40 + q + L, 1.5
+        g = potts.Lattice(L, q, 1, seed)
+        o = oracle.Lattice(L, q, 1, seed)
+        assert np.array_equal(g.sweep(beta, 3), o.sweep(beta, 3)), (L, q)
+        assert np.array_equal(g.spins(), o.spins()), (L, q)
