@@ -320,17 +320,22 @@ TileGeom pass_geom(int32_t nrows, int32_t H, int32_t q, int32_t layout,
     if (q <= 16) g.pairs = 2;
     return g;
   }
+  // 32 sites per thread only on planes of at least 2^23 sites (L >= 4096):
+  // on smaller ones the 16-site walks' twice as many threads fill the GPU
+  // better (L = 1024: 7.6 against 9.6 us per sweep; L = 2048: 11.3 against
+  // 11.7; the same from L = 4096 up)
+  const bool wide_ok = H % 32 == 0 && (int64_t)nrows * H >= (int64_t)1 << 23;
   if (layout == kLayoutU4) {
     // 32 sites (four nibble words, one 16-byte load) per thread and row
-    // where the row allows, else 16
-    TileGeom g = (H % 32 == 0)
+    // where the plane allows, else 16
+    TileGeom g = wide_ok
                      ? choose_geom(nrows, H, q, sm_count, 0, 32, kMinb32)
                      : choose_geom(nrows, H, q, sm_count, 0, 16, kMinbNib);
     g.pairs = 1;
     g.nibble = 1;
     return g;
   }
-  if (H % 32 == 0 && q <= 16) {
+  if (wide_ok && q <= 16) {
     // 32 sites per thread for the cheap q <= 16 rule (1.205 against 1.232
     // ps per update at L = 32768, q = 9; at q = 96 the longer rows are 0.7 %
     // slower); the histogram in (black, white) pair bins on the black pass

@@ -212,7 +212,8 @@ def test_mid_config_protocol(start, ladder_dir):
 
 
 # ------------------------------------------------------- packed 4-bit layout
-U4_CASES = [(32, 2, 1, 0.44, 30), (96, 9, 0, math.log(4.0), 20),
+U4_CASES = [(4096, 16, 0, 40.0, 2),       # 32-site nibble walks, rule LT0
+            (32, 2, 1, 0.44, 30), (96, 9, 0, math.log(4.0), 20),
             (160, 16, 1, 1.3, 15), (544, 15, 1, 1.1, 8), (128, 9, 0, 40.0, 4),
             (128, 6, 1, 0.0, 4), (64, 9, 1, 1.1, 10),
             (4160, 9, 1, workloads.beta_at(9, 1.0), 2)]
@@ -268,3 +269,18 @@ def test_shared_memory_opt_in_across_sizes():
         o = oracle.Lattice(L, q, 1, seed)
         assert np.array_equal(g.sweep(beta, 3), o.sweep(beta, 3)), (L, q)
         assert np.array_equal(g.spins(), o.spins()), (L, q)
+
+
+@pytest.mark.parametrize("L,q,start,beta", [
+    (4096, 2, 1, 0.44), (4096, 16, 0, 40.0), (4096, 9, 1, 0.0),
+    (4160, 9, 1, workloads.beta_at(9, 1.0)),    # 65 chunks of 32 per row
+])
+def test_wide_walks_match_oracle(L, q, start, beta):
+    """Planes of 2^23 sites and more take the 32-site byte walks with the
+    cross-plane histogram (the white pass counts nothing, the black pass
+    both planes): whole-lattice records and spins equal the oracle's."""
+    seed = 7 + q + L
+    g = potts.Lattice(L, q, start, seed)
+    o = oracle.Lattice(L, q, start, seed)
+    assert np.array_equal(g.sweep(beta, 2), o.sweep(beta, 2))
+    assert np.array_equal(g.spins(), o.spins())

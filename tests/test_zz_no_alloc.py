@@ -54,7 +54,8 @@ def _call(dw, db, L, q, seed, t, beta, n, out_ptr, stream):
 
 
 @pytest.mark.parametrize("L,q,use_torch_stream", [(256, 9, False),
-                                                  (544, 24, True)])
+                                                  (544, 24, True),
+                                                  (4096, 9, False)])
 def test_noalloc_equals_oracle_and_allocating_path(L, q, use_torch_stream):
     import torch
     if not torch.cuda.is_available():
