@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kPassThreads,
     for (uint32_t i = tid; i < (uint32_t)kTabWords; i += kPassThreads)
       s_tab[i] = (i % 4u == 0 && i / 4u < 9u) ? sd.tab[i / 4u] : 0u;
   }
-  for (uint32_t v = tid; v < q * kBinStride; v += kPassThreads) s_hist[v] = 0;
+  bins_zero(s_hist, q, tid, kPassThreads);
   if (tid == 0) s_sat = 0;
   if (KIND == kKindHB)
     hb_build_table(s_tab, sd.tab, tid);  // W[0..7]; barrier

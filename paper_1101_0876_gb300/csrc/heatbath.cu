@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kPassThreads, POTTS_HB_MINB)
   constexpr uint32_t STRIDE = kBinStride;  // words per bin (bin_count)
   const uint32_t bins = PBINS ? (uint32_t)kHbPairBins : A.hist_bins;
   if (HIST)
-    for (uint32_t v = tid; v < bins * STRIDE; v += kPassThreads) s_hist[v] = 0;
+    bins_zero(s_hist, bins, tid, kPassThreads);
   if (tid < 16) s_fold[tid] = 0;
   if (tid == 0) s_sat = 0;
   hb_build_table(s_W, T.W, tid);  // ends with a barrier

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kPassThreads,
   for (uint32_t i = tid; i < (uint32_t)kTabWords; i += kPassThreads)
     s_tab[i] = (i % 4u == 0 && i / 4u < 9u) ? Tin.tab[i / 4u] : 0u;
   if (HIST)
-    for (uint32_t v = tid; v < bins * STRIDE; v += kPassThreads) s_hist[v] = 0;
+    bins_zero(s_hist, bins, tid, kPassThreads);
   if (tid < 16) s_fold[tid] = 0;
   if (tid == 0) s_sat = 0;
   __syncthreads();
@@ -126,9 +126,7 @@ __global__ void __launch_bounds__(kPassThreads, NWN == 4 ? kMinb32 : kMinbNib)
   const uint32_t tid = threadIdx.x;
   for (uint32_t i = tid; i < (uint32_t)kTabWords; i += kPassThreads)
     s_tab[i] = (i % 4u == 0 && i / 4u < 9u) ? Tin.tab[i / 4u] : 0u;
-  for (uint32_t v = tid; v < (uint32_t)kPairBins * kBinStride;
-       v += kPassThreads)
-    s_hist[v] = 0;
+  bins_zero(s_hist, kPairBins, tid, kPassThreads);
   if (tid < 16) s_fold[tid] = 0;
   if (tid == 0) s_sat = 0;
   __syncthreads();

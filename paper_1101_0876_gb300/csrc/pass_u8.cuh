@@ -196,6 +196,15 @@ __device__ __forceinline__ uint32_t pack4(uint32_t p0, uint32_t p1,
 // count.
 constexpr uint32_t kBinStride = 64;
 
+// Zeroes the 32 lane counters of bins [0, bins) in the kBinStride layout
+// with 16-byte stores (the other half of each bin's words is never used).
+__device__ __forceinline__ void bins_zero(uint32_t *s_hist, uint32_t bins,
+                                          uint32_t tid, uint32_t nthreads) {
+  for (uint32_t v = tid; v < bins * 8u; v += nthreads)
+    *reinterpret_cast<uint4 *>(s_hist + (v >> 3) * kBinStride + (v & 7u) * 4u) =
+        make_uint4(0u, 0u, 0u, 0u);
+}
+
 // Counts bin (byte b of t) in the calling lane's counters; s_hist: the CTA's
 // counters (kBinStride words a bin).
 __device__ __forceinline__ void bin_count(uint32_t *s_hist, uint32_t t,
